@@ -1,0 +1,244 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test checks the oracle against a fact that the paper or the mathematics fixes:
+  * one oracle iteration == one generic scaled-form ADMM pass on the velocity-form splitting,
+    built as explicit F, G, h (Theorem 2's problem) and solved by dense least squares and BVLS;
+  * the converged iterate == the KKT point of the MPC QP found by brute-force active-set
+    enumeration (tiny LTV), and == the equality-constrained closed form when no bound is active;
+  * invariants: c non-increasing for plain ADMM (He & Yuan, Thm 4.1), z always in the box, fixed
+    point at convergence, rho-independence of the optimum, u_prev-independence when W_du = 0,
+    accelerated mode with eta = 0 reduces to the plain iteration;
+  * a scalar case computed by hand.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import qp_reference as qp
+
+
+def tiny_ltv(seed, nx=2, nu=1, N=3, xabs=2.0, uabs=0.5, rdu=False, ref_scale=0.0, x0_abs=2.5):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((N, nx, nx)) * 0.6
+    B = rng.standard_normal((N, nx, nu))
+    e = rng.uniform(-0.2, 0.2, (N, nx))
+    n = nx + nu
+    return dict(nx=nx, nu=nu, N=N, lti=False, A=A, B=B, e=e,
+                q=rng.uniform(0.5, 2.0, nx), r=rng.uniform(0.1, 1.0, nu),
+                rdu=rng.uniform(0.05, 0.5, nu) if rdu else None,
+                xmin=-xabs * np.ones(nx), xmax=xabs * np.ones(nx),
+                umin=-uabs * np.ones(nu), umax=uabs * np.ones(nu),
+                x0=rng.uniform(-x0_abs, x0_abs, nx),
+                u_prev=rng.uniform(-uabs, uabs, nu),
+                ref=ref_scale * rng.standard_normal((N, n)), rho=float(rng.uniform(0.5, 2.0)))
+
+
+# ---------------------------------------------------------------------------------------------
+# One iteration against the generic scaled ADMM on explicit F, G, h.
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,rdu,hat_scale,bound", [
+    (0, False, 0.3, 5.0),   # nothing clamps
+    (1, True, 0.3, 5.0),    # with an input-increment weight
+    (2, False, 3.0, 0.4),   # many components clamp
+    (3, True, 3.0, 0.4),
+    (4, False, 1.0, 1.0),
+])
+def test_one_iteration_equals_generic_admm(seed, rdu, hat_scale, bound):
+    inst = tiny_ltv(seed, nx=3, nu=2, N=4, xabs=bound, uabs=bound, rdu=rdu, ref_scale=1.0)
+    N, nx, nu = inst["N"], inst["nx"], inst["nu"]
+    n = nx + nu
+    rng = np.random.default_rng(100 + seed)
+    hats = {k: hat_scale * rng.standard_normal((N, n)) for k in ("z", "v", "th", "be", "la")}
+    H, J = oracle.cache(inst)
+    out = oracle.iteration(inst, H, J, hats)
+
+    sys_ = qp.velocity_FGh(inst)
+    qhat = np.concatenate([hats["v"].ravel(), hats["z"].ravel()])
+    shat = np.concatenate([hats["th"].ravel(), hats["be"].ravel(), hats["la"].ravel()])
+    p, q, s, c = qp.generic_admm_step(sys_, inst["rho"], qhat, shat)
+
+    np.testing.assert_allclose(out["du"].ravel(), p[: N * nu], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(out["xb"].ravel(), p[N * nu:], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(out["v"].ravel(), q[: N * n], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(out["z"].ravel(), q[N * n:], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(out["th"].ravel(), s[: N * n], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(out["be"].ravel(), s[N * n: 2 * N * n], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(out["la"].ravel(), s[2 * N * n:], rtol=0, atol=1e-10)
+    assert abs(out["c"] - c) <= 1e-10 * max(1.0, c)
+    if bound < 1.0:
+        z = out["z"]
+        lo = np.concatenate([inst["xmin"], inst["umin"]])
+        hi = np.concatenate([inst["xmax"], inst["umax"]])
+        assert np.sum(np.isclose(z, lo) | np.isclose(z, hi)) >= 5  # the projection really acted
+
+
+# ---------------------------------------------------------------------------------------------
+# Converged solution against brute-force KKT enumeration and the equality-constrained form.
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,rdu", [(7, False), (18, False), (16, True), (8, True)])
+def test_converged_equals_kkt_enumeration(seed, rdu):
+    inst = tiny_ltv(seed, nx=2, nu=1, N=3, xabs=1.5, uabs=0.4, rdu=rdu, ref_scale=0.5)
+    P, c, Aeq, beq, lb, ub, idx = qp.original_qp(inst)
+    cands = qp.kkt_enumerate(P, c, Aeq, beq, lb, ub)
+    assert len(cands) >= 1
+    ystar = cands[0][0]
+    for y, _ in cands[1:]:  # degenerate duplicates must be the same point
+        np.testing.assert_allclose(y, ystar, atol=1e-8)
+    n_active = int(np.sum(np.isclose(ystar, lb, atol=1e-9) | np.isclose(ystar, ub, atol=1e-9)))
+    assert n_active >= 1, "fixture must have active bounds"
+    N = inst["N"]
+    for accel in (0, 1):
+        res = oracle.solve(inst, eps=1e-26, max_iters=400000, accel=accel)
+        y = np.zeros_like(ystar)
+        for k in range(N):
+            y[idx(k, "u")] = res["u"][k]
+            y[idx(k, "x")] = res["x"][k]
+        np.testing.assert_allclose(y, ystar, rtol=0, atol=1e-8)
+
+
+def test_unbounded_equals_equality_qp():
+    inst = tiny_ltv(21, nx=4, nu=2, N=20, ref_scale=1.0)
+    for key in ("xmin", "umin"):
+        inst[key] = -np.inf * np.ones_like(inst[key])
+    for key in ("xmax", "umax"):
+        inst[key] = np.inf * np.ones_like(inst[key])
+    P, c, Aeq, beq, lb, ub, idx = qp.original_qp(inst)
+    ystar, _ = qp.equality_qp(P, c, Aeq, beq)
+    res = oracle.solve(inst, eps=1e-26, max_iters=200000, accel=1)
+    y = np.zeros_like(ystar)
+    for k in range(inst["N"]):
+        y[idx(k, "u")] = res["u"][k]
+        y[idx(k, "x")] = res["x"][k]
+    np.testing.assert_allclose(y, ystar, rtol=0, atol=1e-9 * max(1.0, np.abs(ystar).max()))
+
+
+# ---------------------------------------------------------------------------------------------
+# Invariants.
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_plain_residual_is_monotone(seed):
+    # He & Yuan (2015), Thm 4.1: c^{i+1} <= c^i for the plain iteration.
+    inst = tiny_ltv(seed, x0_abs=0.8, nx=3, nu=2, N=12, xabs=1.0, uabs=0.3, ref_scale=1.0)
+    res = oracle.solve(inst, eps=-1.0, max_iters=400, accel=0, history=True)
+    ch = res["c_hist"]
+    assert np.all(ch[1:] <= ch[:-1] * (1 + 1e-9) + 1e-300)
+
+
+def test_z_stays_in_box_every_iteration():
+    inst = tiny_ltv(41, x0_abs=0.8, nx=3, nu=2, N=8, xabs=0.8, uabs=0.2, ref_scale=2.0)
+    lo = np.concatenate([inst["xmin"], inst["umin"]])
+    hi = np.concatenate([inst["xmax"], inst["umax"]])
+    for K in (1, 2, 3, 7, 20, 61):
+        for accel in (0, 1):
+            res = oracle.solve(inst, eps=-1.0, max_iters=K, accel=accel)
+            assert np.all(res["z"] >= lo) and np.all(res["z"] <= hi)
+
+
+def test_fixed_point_and_dynamics_at_convergence():
+    inst = tiny_ltv(51, x0_abs=0.8, nx=3, nu=2, N=10, xabs=1.0, uabs=0.3, ref_scale=1.0)
+    res = oracle.solve(inst, eps=1e-28, max_iters=300000, accel=1)
+    assert res["status"] == oracle.CONVERGED
+    H, J = oracle.cache(inst)
+    out = oracle.iteration(inst, H, J, res)
+    for k in ("z", "v", "th", "be", "la"):
+        np.testing.assert_allclose(out[k], res[k], rtol=0, atol=1e-11)
+    # xbar = z, Bbar du = v, and xbar_{k+1} = Abar_k xbar_k + Bbar_k du_k + ebar_k at the optimum
+    nx, nu = inst["nx"], inst["nu"]
+    np.testing.assert_allclose(out["xb"], out["z"], atol=1e-10)
+    xprev = np.concatenate([inst["x0"], inst["u_prev"]])
+    for k in range(inst["N"]):
+        A, B, e = inst["A"][k], inst["B"][k], inst["e"][k]
+        x_next = A @ xprev[:nx] + B @ (xprev[nx:] + out["du"][k]) + e
+        np.testing.assert_allclose(out["xb"][k, :nx], x_next, atol=1e-10)
+        np.testing.assert_allclose(out["xb"][k, nx:], xprev[nx:] + out["du"][k], atol=1e-10)
+        xprev = out["xb"][k]
+
+
+def test_optimum_independent_of_rho():
+    inst = tiny_ltv(61, x0_abs=0.8, nx=3, nu=2, N=10, xabs=1.0, uabs=0.3, ref_scale=1.0)
+    sols = []
+    for rho in (0.3, 1.0, 4.0):
+        inst["rho"] = rho
+        res = oracle.solve(inst, eps=1e-26, max_iters=400000, accel=1)
+        sols.append(np.concatenate([res["u"].ravel(), res["x"].ravel()]))
+    np.testing.assert_allclose(sols[0], sols[1], atol=1e-8)
+    np.testing.assert_allclose(sols[0], sols[2], atol=1e-8)
+
+
+def test_optimum_independent_of_u_prev_without_du_weight():
+    inst = tiny_ltv(71, x0_abs=0.8, nx=3, nu=2, N=10, xabs=1.0, uabs=0.3, ref_scale=1.0)
+    a = oracle.solve(inst, eps=1e-26, max_iters=400000, accel=1)
+    inst["u_prev"] = np.array([0.25, -0.1])
+    b = oracle.solve(inst, eps=1e-26, max_iters=400000, accel=1)
+    np.testing.assert_allclose(a["u"], b["u"], atol=1e-8)
+    np.testing.assert_allclose(a["x"], b["x"], atol=1e-8)
+
+
+def test_accel_with_eta_zero_is_plain():
+    # eta = 0: the momentum branch needs c <= 0, so every step restarts and hats = iterates.
+    inst = tiny_ltv(81, x0_abs=0.8, nx=3, nu=2, N=9, xabs=1.0, uabs=0.3, ref_scale=1.0)
+    a = oracle.solve(inst, eps=-1.0, max_iters=150, accel=0)
+    b = oracle.solve(inst, eps=-1.0, max_iters=150, accel=1, eta=0.0)
+    for k in ("z", "v", "th", "be", "la"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_accel_converges_faster_than_plain():
+    inst = tiny_ltv(91, x0_abs=0.8, nx=3, nu=2, N=30, xabs=2.0, uabs=0.5, ref_scale=1.0)
+    a = oracle.solve(inst, eps=1e-12, max_iters=200000, accel=0)
+    b = oracle.solve(inst, eps=1e-12, max_iters=200000, accel=1)
+    assert a["status"] == oracle.CONVERGED and b["status"] == oracle.CONVERGED
+    assert b["iters"] < a["iters"]
+
+
+def test_forced_mask_replays_decisions():
+    inst = tiny_ltv(95, x0_abs=0.8, nx=3, nu=2, N=9, xabs=1.0, uabs=0.3, ref_scale=1.0)
+    a = oracle.solve(inst, eps=-1.0, max_iters=120, accel=1, history=True)
+    b = oracle.solve(inst, eps=-1.0, max_iters=120, accel=1, force_mask=a["mask"])
+    assert a["mask"].any() and not a["mask"].all()
+    for k in ("z", "v", "th", "be", "la"):
+        assert np.array_equal(a[k], b[k])
+
+
+# ---------------------------------------------------------------------------------------------
+# A scalar case computed by hand (nx = nu = 1, N = 1, plain iteration from zero).
+# ---------------------------------------------------------------------------------------------
+
+def test_scalar_case_by_hand():
+    inst = dict(nx=1, nu=1, N=1, lti=True, A=np.array([[0.5]]), B=np.array([[1.0]]),
+                e=np.array([0.25]), q=np.array([1.0]), r=np.array([1.0]), rdu=None,
+                xmin=np.array([-10.0]), xmax=np.array([10.0]), umin=np.array([-0.1]),
+                umax=np.array([0.1]), x0=np.array([2.0]), u_prev=None,
+                ref=np.array([1.0, 1.0]), rho=1.0)
+    # Iteration 1 (all hats 0): du = 0; H = (Qbar + I)^-1 = I/2, h = Qbar ref = (1, 1), so
+    # xbar_1 = (0.5, 0.5). Abar xbar_0 = (0.5*2 + 1*0, 0) = (1, 0), ebar = (0.25, 0).
+    # gamma = (-1.25, 0); w = ((2*(0.5+1+0.25) - 1.25)/3, (2*0.5)/3) = (0.75, 1/3) -> z = (0.75, 0.1)
+    # v = (z + gamma)/2 = (-0.25, 0.05); theta = xbar - z = (-0.25, 0.4); beta = -v = (0.25, -0.05)
+    # lambda = z - Abar xbar_0 - v - ebar = (-0.25, 0.05)
+    # c = (0.0625*4 + 0.5625 + 1) + (0.16 + 0.0025*4 + 0.01) = 1.8125 + 0.18 = 1.9925
+    r1 = oracle.solve(inst, eps=-1.0, max_iters=1)
+    np.testing.assert_allclose(r1["z"], [[0.75, 0.1]], atol=1e-15)
+    np.testing.assert_allclose(r1["v"], [[-0.25, 0.05]], atol=1e-15)
+    np.testing.assert_allclose(r1["th"], [[-0.25, 0.4]], atol=1e-15)
+    np.testing.assert_allclose(r1["be"], [[0.25, -0.05]], atol=1e-15)
+    np.testing.assert_allclose(r1["la"], [[-0.25, 0.05]], atol=1e-15)
+    np.testing.assert_allclose(r1["xb"], [[0.5, 0.5]], atol=1e-15)
+    assert abs(r1["c"] - 1.9925) < 1e-14
+    # Iteration 2 (hats = iteration-1 iterates): J = (Bbar'Bbar)^-1 Bbar' = (1/2, 1/2),
+    # du = ((-0.25-0.25) + (0.05+0.05))/2 = -0.2; h = (1 + 0.75 + 0.25, 1 + 0.1 - 0.4) = (2, 0.7),
+    # xbar_1 = (1, 0.35); Bbar du = (-0.2, -0.2); gamma = (-1.45, -0.2);
+    # w = ((2*2.25 - 1.45)/3, (2*0.7 - 0.2)/3) = (61/60, 0.4) -> z = (61/60, 0.1)
+    # v = (-13/60, -0.05); theta = (-4/15, 0.65); beta = (4/15, -0.2); lambda = (-4/15, 0.2)
+    # c = 459/3600 + 0.1275 = 0.255
+    r2 = oracle.solve(inst, eps=-1.0, max_iters=2)
+    np.testing.assert_allclose(r2["du"], [[-0.2]], atol=1e-15)
+    np.testing.assert_allclose(r2["xb"], [[1.0, 0.35]], atol=1e-15)
+    np.testing.assert_allclose(r2["z"], [[61 / 60, 0.1]], atol=1e-15)
+    np.testing.assert_allclose(r2["v"], [[-13 / 60, -0.05]], atol=1e-15)
+    np.testing.assert_allclose(r2["th"], [[-4 / 15, 0.65]], atol=1e-15)
+    np.testing.assert_allclose(r2["be"], [[4 / 15, -0.2]], atol=1e-15)
+    np.testing.assert_allclose(r2["la"], [[-4 / 15, 0.2]], atol=1e-15)
+    assert abs(r2["c"] - 0.255) < 1e-14
