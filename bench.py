@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the piMPC hot path (arXiv 2601.14414) on GB300: batched uneven NMPC/MPC solves.
+
+Workload (per GPU): 4096 independent random linear time-varying MPC instances, nx ~ U{4..24},
+nu ~ U{2..8}, N ~ U{50..500} (1.13M stages), FP32 ADMM iterations of Algorithm 1 (accelerated,
+with restart) on an FP64 per-stage factorisation, one persistent launch for the whole batch.
+
+One step = factorise (FP64 cache of Algorithm 1) + solve (all iterations of every instance), cold
+start, inputs resident in HBM. A solve counts when its (u, x) is within 1e-4 (max error over
+max(1, max|w*|)) of the FP64 solution of the same instance from this GPU's FP64 path run to
+c <= 1e-15. The stage data (~3.5 GB) is far larger than the 129 MB L2, so no flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank solves its own seeded batch (weak scaling, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "batched NMPC solves/s & ADMM iters/s at 1e-4 vs FP64 plain path; % roofline"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=None, help="instances per GPU (default 4096)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6],
+                                 swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                          ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+            if any(r[key].lower().startswith("active") for r in rows):
+                reasons.append(name)
+        return dict(sm_mhz=float(np.median([r["sm"] for r in rows])),
+                    sm_max_mhz=float(max(r["smax"] for r in rows)), reasons=reasons,
+                    samples=len(rows))
+
+
+def gpu_uuid(torch):
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------------------------
+# Algorithmic work (per stage-iteration; the per-unit figures stated in the design doc).
+# ---------------------------------------------------------------------------------------------
+
+def matrix_words(nx, nu):
+    n = nx + nu
+    return nx * n + nx + n * (n + 1) // 2 + nu * (nu + 1) // 2
+
+
+def algorithmic_bytes(nx, nu, N, iters, momentum, word):
+    """Minimum HBM traffic of the solve: per stage and iteration the stage matrices (G_k, e_k,
+    packed H_k and M_k) plus the iterates: read z, v, theta, beta, lambda (5n), write them (5n),
+    and read the previous iterate too (5n) on iterations that use the momentum step."""
+    n = nx + nu
+    per_stage = matrix_words(nx, nu) + 10 * n
+    return float(np.sum(N * (iters * per_stage + momentum * 5 * n)) * word)
+
+
+def load_peaks():
+    path = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    src = os.path.join(HERE, "paper_2601_14414_gb300", "csrc", "admm.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(profile_name):
+    """DRAM bytes per launch of the ADMM kernel from the committed ncu summary, if it was taken on
+    the current kernel source (its admm.cu hash matches); else None."""
+    path = os.path.join(HERE, "profiles", profile_name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"admm\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_traffic = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+-]+)", text)
+    if not m_hash or not m_traffic or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_traffic.group(1))
+
+
+# ---------------------------------------------------------------------------------------------
+# The reference arm: the FP64 CPU oracle on the host cores.
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample(insts, cfg, seconds_hint, rng_seed=0):
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(rng_seed)
+    order = rng.permutation(len(insts))
+    # Grow the sample until it takes about `seconds_hint` seconds on all host cores.
+    take = max(threads, 8)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        chunk = [insts[i] for i in order[done:done + take]]
+        if not chunk:
+            break
+        oracle.solve_batch(chunk, threads=threads, eps=cfg["eps"], max_iters=cfg["max_iters"],
+                           accel=cfg["accel"], eta=cfg["eta"])
+        done += len(chunk)
+        if time.perf_counter() - t0 >= seconds_hint:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, threads
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2601_14414_gb300 import configs, workloads as W
+    cfg = configs.BATCHED_UNEVEN
+    batch = args.batch or cfg["batch"]
+    insts = W.batched_uneven(seed=cfg["seed"], batch=batch)
+    for _ in range(args.warmup):
+        oracle_sample(insts[:0], cfg, 0.0)
+    times, counts, threads = [], [], 1
+    for k in range(args.steps):
+        n, dt, threads = oracle_sample(insts, cfg, 20.0, rng_seed=k)
+        times.append(dt)
+        counts.append(n)
+    value = float(np.sum(counts) / np.sum(times))
+    line = dict(impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * float(np.mean(times)), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=cfg["name"], instances=batch, eps=cfg["eps"],
+                            accel=cfg["accel"], max_iters=cfg["max_iters"]),
+                cpu_baseline=dict(value=value, unit="solves/s", cores=threads, kind="oracle",
+                                  sample=f"{int(np.mean(counts))} random instances of the "
+                                         f"{batch}-instance workload per step"),
+                e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# Our arm.
+# ---------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    from paper_2601_14414_gb300 import configs, pimpc, workloads as W
+    cfg = configs.BATCHED_UNEVEN
+    batch = args.batch or cfg["batch"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    insts = W.batched_uneven(seed=cfg["seed"] + 7919 * rank, batch=batch)
+    p = pimpc.pack(insts)
+    nx, nu, N = p["nx"].astype(np.int64), p["nu"].astype(np.int64), p["N"].astype(np.int64)
+    d = {k: torch.from_numpy(p[k]).to(dev) for k in ("A", "B", "e", "x0", "ref")}
+    tot_u, tot_x = int(np.sum(N * nu)), int(np.sum(N * nx))
+
+    def make(prec, eps, iters):
+        h = pimpc.pimpc_create(p["nx"], p["nu"], p["N"], 0, prec, device=dev.index)
+        pimpc.pimpc_set_weights(h, p["q"], p["r"], p["rdu"])
+        pimpc.pimpc_set_bounds(h, p["xmin"], p["xmax"], p["umin"], p["umax"])
+        pimpc.pimpc_set_options(h, cfg["rho"], eps, iters, cfg["accel"], cfg["eta"])
+        pimpc.pimpc_set_dynamics(h, d["A"], d["B"], d["e"])
+        return h
+
+    # FP64 reference solution on this GPU (untimed), scored against in every step.
+    href = make(pimpc.F64, cfg["ref_eps"], cfg["ref_max_iters"])
+    u_ref = torch.zeros(tot_u, dtype=torch.float64, device=dev)
+    x_ref = torch.zeros(tot_x, dtype=torch.float64, device=dev)
+    pimpc.pimpc_solve(href, d["x0"], None, d["ref"], p["ref_per_stage"], 0, u_ref, x_ref)
+    torch.cuda.synchronize()
+    pimpc.pimpc_destroy(href)
+
+    h = make(pimpc.F32, cfg["eps"], cfg["max_iters"])
+    u = torch.zeros(tot_u, dtype=torch.float64, device=dev)
+    x = torch.zeros(tot_x, dtype=torch.float64, device=dev)
+
+    def step(ev_a=None, ev_b=None, ev_c=None):
+        if ev_a is not None:
+            ev_a.record(stream)
+        pimpc.pimpc_factorise(h, stream.cuda_stream)
+        if ev_b is not None:
+            ev_b.record(stream)
+        pimpc.pimpc_solve(h, d["x0"], None, d["ref"], p["ref_per_stage"], 0, u, x)
+        if ev_c is not None:
+            ev_c.record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(gpu_uuid(torch))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(*evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    fact_ms = [a.elapsed_time(b) for a, b, _ in evs]
+    solve_ms = [b.elapsed_time(c) for _, b, c in evs]
+
+    # Per-instance results of the last step.
+    iters = np.zeros(batch, np.int32)
+    cvals = np.zeros(batch)
+    status = np.zeros(batch, np.int32)
+    mom = np.zeros(batch, np.int32)
+    pimpc.pimpc_get_stats(h, iters, cvals, status, mom)
+    uu, xx, ur, xr = (t.cpu().numpy() for t in (u, x, u_ref, x_ref))
+    ou = np.concatenate([[0], np.cumsum(N * nu)])
+    ox = np.concatenate([[0], np.cumsum(N * nx)])
+    err = np.zeros(batch)
+    for j in range(batch):
+        w = np.concatenate([uu[ou[j]:ou[j + 1]], xx[ox[j]:ox[j + 1]]])
+        ws = np.concatenate([ur[ou[j]:ou[j + 1]], xr[ox[j]:ox[j + 1]]])
+        err[j] = np.max(np.abs(w - ws)) / max(1.0, np.max(np.abs(ws)))
+    ok = int(np.sum(err <= cfg["accuracy"]))
+
+    ms_step = total_ms / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step, ok, float(np.sum(iters)), float(np.sum(iters * N))],
+                         dtype=torch.float64, device=dev)
+        allt = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(allt, t)
+        allt = torch.stack(allt).cpu().numpy()
+        ms_max = float(allt[:, 0].max())
+        ok_all, it_all, stit_all = (float(allt[:, i].sum()) for i in (1, 2, 3))
+    else:
+        ms_max, ok_all, it_all, stit_all = ms_step, ok, float(np.sum(iters)), float(np.sum(iters * N))
+    value = ok_all / (ms_max / 1e3)
+
+    # Roofline of the dominant kernel (the ADMM solve), bytes per launch / launch time.
+    alg = algorithmic_bytes(nx, nu, N, iters.astype(np.int64), mom.astype(np.int64), 4)
+    solve_s = float(np.mean(solve_ms)) / 1e3
+    peak, peak_kind = load_peaks()
+    achieved = alg / solve_s / 1e9
+    traffic = profiled_traffic("admm_batched_uneven_ltv_4096.md")
+
+    line = None
+    if rank == 0:
+        # e2e: the same step through the C ABI with host buffers (pinned), copies inside.
+        e2e = None
+        if not args.no_e2e:
+            pinned = {k: torch.from_numpy(p[k]).pin_memory() for k in ("A", "B", "e", "x0", "ref")}
+            hp = {k: v.numpy() for k, v in pinned.items()}
+            hu = torch.zeros(tot_u, dtype=torch.float64).pin_memory().numpy()
+            hx = torch.zeros(tot_x, dtype=torch.float64).pin_memory().numpy()
+            hit = np.zeros(batch, np.int32)
+            hst = np.zeros(batch, np.int32)
+            he = make(pimpc.F32, cfg["eps"], cfg["max_iters"])
+
+            def host_step():
+                pimpc.pimpc_set_dynamics(he, hp["A"], hp["B"], hp["e"])
+                pimpc.pimpc_solve(he, hp["x0"], None, hp["ref"], p["ref_per_stage"], 0, hu, hx,
+                                  hit, None, hst)
+
+            for _ in range(max(1, min(args.warmup, 2))):
+                host_step()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                host_step()
+            torch.cuda.synchronize()
+            e2e_s = (time.perf_counter() - t0) / args.steps
+            w_all = np.concatenate([hu, hx])
+            same = np.array_equal(hu, uu) and np.array_equal(hx, xx)
+            h2d = sum(hp[k].nbytes for k in ("A", "B", "e", "x0", "ref"))
+            d2h = hu.nbytes + hx.nbytes + hit.nbytes + hst.nbytes
+            e2e = dict(value=ok / e2e_s, unit="solves/s", h2d_bytes_per_step=int(h2d),
+                       d2h_bytes_per_step=int(d2h), ms_per_step=1e3 * e2e_s,
+                       same_result_as_device_path=bool(same))
+            pimpc.pimpc_destroy(he)
+            del w_all
+
+        # The plain single-instance FP64 GPU path on a sample of the same instances.
+        rng = np.random.default_rng(0)
+        sample = rng.choice(batch, size=16, replace=False)
+        t_single = 0.0
+        ok_single = 0
+        for j in sample:
+            inst = insts[j]
+            s1 = pimpc.Solver([inst], precision=pimpc.F64, eps=cfg["eps"],
+                              max_iters=cfg["max_iters"], accel=cfg["accel"], eta=cfg["eta"])
+            s1.solve()  # warm-up of this object
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r1 = s1.solve()
+            t_single += time.perf_counter() - t0
+            w = np.concatenate([r1["u"][0].ravel(), r1["x"][0].ravel()])
+            ws = np.concatenate([ur[ou[j]:ou[j + 1]], xr[ox[j]:ox[j + 1]]])
+            ok_single += int(np.max(np.abs(w - ws)) / max(1.0, np.max(np.abs(ws))) <= cfg["accuracy"])
+            s1.close()
+        single = dict(value=ok_single / t_single, unit="solves/s", sample=int(len(sample)),
+                      note="one FP64 instance per solver object and launch, same eps, accel")
+
+        cpu = None
+        if not args.no_cpu_baseline:
+            n_cpu, dt_cpu, cores = oracle_sample(insts, cfg, 20.0)
+            cpu = dict(value=n_cpu / dt_cpu, unit="solves/s", cores=cores, kind="oracle",
+                       sample=f"{n_cpu} random instances of the {batch}-instance workload "
+                              f"(all iterations to the same eps), {dt_cpu:.1f} s")
+
+        n_stages = int(np.sum(N))
+        stage_bytes = float(np.sum(N * (matrix_words(nx, nu) + 10 * (nx + nu)))) * 4
+        line = dict(
+            metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps,
+            warmup=args.warmup, ms_per_step=ms_max, higher_is_better=True, scaling="weak",
+            vs_baseline=None, dtype="f32", data="synthetic",
+            config=dict(workload=cfg["name"], instances_per_gpu=batch, stages_per_gpu=n_stages,
+                        nx="4..24", nu="2..8", N="50..500", eps=cfg["eps"], accel=cfg["accel"],
+                        max_iters=cfg["max_iters"], factorisation="fp64",
+                        l2="no flush: stage data %.1f GB per GPU >> 129 MB L2" % (stage_bytes / 1e9),
+                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            iters_per_s=it_all / (ms_max / 1e3),
+            stage_iters_per_s=stit_all / (ms_max / 1e3),
+            accuracy=dict(ok=ok, of=batch, threshold=cfg["accuracy"],
+                          median_err=float(np.median(err)), max_err=float(np.max(err)),
+                          converged=int(np.sum(status == pimpc.CONVERGED)),
+                          mean_iters=float(np.mean(iters))),
+            breakdown_ms=dict(factorise=float(np.mean(fact_ms)), solve=float(np.mean(solve_ms))),
+            roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
+                          frac=achieved / peak, traffic=traffic,
+                          kernel="admm_kernel<float>", peak_kind=peak_kind,
+                          algorithmic_bytes_per_launch=alg),
+            fp64_single_instance_gpu=single,
+            cpu_baseline=cpu,
+            e2e=e2e,
+            gpu_launches=4 * args.steps,
+            clocks=clk,
+        )
+        print(json.dumps(line), flush=True)
+    pimpc.pimpc_destroy(h)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,223 @@
+/*
+ * pimpc.h -- C ABI of the GB300 (sm_103a) piMPC solver library.
+ *
+ * The library runs the hot path of piMPC (Wu et al., "piMPC: A Parallel-in-horizon and
+ * Construction-free NMPC Solver", arXiv 2601.14414): the velocity-form, construction-free ADMM
+ * iteration of Algorithm 1 on a batch of independent MPC instances, plus the real-time-iteration
+ * pieces around it (explicit-Euler relinearisation, the per-stage factorisations the iteration
+ * caches, the plant step) and a reverse-mode adjoint of the unrolled iteration.
+ *
+ * Problem (Sec. II, problem statement): for each instance
+ *   min  sum_k 1/2 ||x_{k+1} - r_x||^2_Q + 1/2 ||u_k - r_u||^2_R  (+ 1/2 ||u_k - u_{k-1}||^2_Wdu)
+ *   s.t. x_{k+1} = A_k x_k + B_k u_k + e_k,  xmin <= x_{k+1} <= xmax,  umin <= u_k <= umax,
+ *        x_0 = x(t),  k = 0..N-1,
+ * with Q, R, Wdu diagonal (C = I). The solver works on the velocity form of Theorem 2,
+ * xbar_k = (x_k, u_{k-1}), n = nx + nu.
+ *
+ * Conventions for every call:
+ *   - Plain C types only. Every array argument is FP64, row-major, instances concatenated in
+ *     batch order, each instance's part stage-major. `mem` says whether the pointers are host
+ *     (PIMPC_HOST) or device (PIMPC_DEVICE) memory of the solver's device. `stream` is a
+ *     cudaStream_t (NULL = legacy default stream); device-memory calls are asynchronous on it;
+ *     host-memory calls copy with cudaMemcpyAsync on it and synchronise it before returning.
+ *   - Ownership: the caller owns every buffer it passes and may free or reuse it when the call
+ *     returns (host memory) or when the stream has passed the call (device memory). The solver
+ *     owns all device state (matrices, caches, iterates); pimpc_create allocates all of it
+ *     except the adjoint's checkpoint store, which the first pimpc_backward call allocates, and
+ *     the buffer of the testing aid pimpc_set_restart_mask; pimpc_destroy frees everything.
+ *   - Errors: a nonzero return means the call did nothing (arguments are validated before any
+ *     launch) except PIMPC_ECUDA, which reports a CUDA error; pimpc_last_error(s) then holds a
+ *     message. Non-convergence is not an error: it is reported per instance in `status`.
+ *   - One solver object serves one stream at a time; calls on one object are not thread-safe.
+ */
+#ifndef PIMPC_H
+#define PIMPC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+enum { PIMPC_OK = 0, PIMPC_EINVAL = 1, PIMPC_ENOMEM = 2, PIMPC_ECUDA = 3, PIMPC_ESTATE = 4 };
+/* Per-instance solve status. */
+enum { PIMPC_CONVERGED = 0, PIMPC_MAXITER = 1, PIMPC_NONFINITE = 2, PIMPC_TIMEOUT = 3 };
+/* Arithmetic of the ADMM iterations (the factorisation is always FP64). */
+enum { PIMPC_F32 = 0, PIMPC_F64 = 1 };
+/* Memory space of caller buffers. */
+enum { PIMPC_HOST = 0, PIMPC_DEVICE = 1 };
+/* Built-in nonlinear models for pimpc_linearise / pimpc_plant_step. */
+enum { PIMPC_MODEL_QUADROTOR = 0, PIMPC_MODEL_CARTPOLE = 1, PIMPC_MODEL_CSTR = 2 };
+
+/* Size limits of one instance. */
+#define PIMPC_MAX_N_LTV 32   /* n = nx + nu for stage-varying dynamics   */
+#define PIMPC_MAX_N_LTI 64   /* n = nx + nu for stage-invariant dynamics */
+
+typedef struct pimpc_solver pimpc_solver;
+
+/*
+ * pimpc_create -- setup(model dims, N): allocate a solver for `batch` independent instances.
+ *   nx[batch], nu[batch], N[batch]  host arrays: state size (>= 1), input size (>= 1) and horizon
+ *                                   (>= 1) of each instance; n = nx + nu <= PIMPC_MAX_N_LTV
+ *                                   (lti = 0) or PIMPC_MAX_N_LTI (lti = 1).
+ *   lti        1: one (A, B, e) per instance used at every stage; 0: one triple per stage.
+ *   precision  PIMPC_F32 or PIMPC_F64 arithmetic for the iterations.
+ *   device     CUDA device ordinal.
+ *   out        receives the solver (NULL on failure).
+ * Defaults after create: rho = 1, eps = 1e-6, max_iters = 1000, accel = 1, eta = 0.999
+ * (Algorithm 1), zero weights, infinite bounds, zero dynamics, cold start.
+ * Errors: PIMPC_EINVAL (sizes), PIMPC_ENOMEM, PIMPC_ECUDA. On failure the message is returned
+ * by pimpc_last_error(NULL) on the calling thread.
+ */
+int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti, int precision,
+                 int device, pimpc_solver **out);
+
+/* Free all device and host memory of the solver; synchronises its last stream. NULL is a no-op. */
+void pimpc_destroy(pimpc_solver *s);
+
+/* Message of the last failed call on `s` ("" if none); with s == NULL, of the last failed
+ * pimpc_create on this thread. The string lives until the next call on the same object. */
+const char *pimpc_last_error(const pimpc_solver *s);
+
+/*
+ * pimpc_set_weights -- setup(Q, R): cost weights Qbar = diag(q, r) of Theorem 2.
+ *   q[sum nx]    diagonal of C^T W_y C (>= 0);  r[sum nu] diagonal of W_u (>= 0);
+ *   rdu[sum nu]  diagonal of an optional weight on u_k - u_{k-1} (>= 0), NULL = 0 (Algorithm 1).
+ * Marks the factorisation stale. Errors: PIMPC_EINVAL for a negative or non-finite entry.
+ */
+int pimpc_set_weights(pimpc_solver *s, const double *q, const double *r, const double *rdu,
+                      int mem, void *stream);
+
+/*
+ * pimpc_set_bounds -- setup(bounds): the box Xbar = X x U of Theorem 2, same for every stage.
+ *   xmin, xmax [sum nx]; umin, umax [sum nu]; +-INFINITY allowed, NaN not.
+ * Errors: PIMPC_EINVAL if some lower bound exceeds its upper bound.
+ */
+int pimpc_set_bounds(pimpc_solver *s, const double *xmin, const double *xmax, const double *umin,
+                     const double *umax, int mem, void *stream);
+
+/*
+ * pimpc_set_options -- setup(rho) and the iteration controls of Algorithm 1.
+ *   rho > 0 (penalty; a change marks the factorisation stale), eps (stop when c^{i+1} <= eps,
+ *   step 5; eps < 0 never stops early), max_iters >= 0 (K_max), accel (0: plain iteration,
+ *   1: accelerated with restart, steps 6-7), eta (restart threshold, 0.999 in Algorithm 1).
+ * Errors: PIMPC_EINVAL.
+ */
+int pimpc_set_options(pimpc_solver *s, double rho, double eps, int max_iters, int accel,
+                      double eta);
+
+/*
+ * pimpc_set_dynamics -- construction-free input: the stage matrices themselves (Sec. II).
+ *   A [sum N nx nx] (lti: [sum nx nx]), B [sum N nx nu] (lti: [sum nx nu]),
+ *   e [sum N nx] (lti: [sum nx]); e may be NULL (= 0).
+ * Marks the factorisation stale. Errors: PIMPC_EINVAL.
+ */
+int pimpc_set_dynamics(pimpc_solver *s, const double *A, const double *B, const double *e,
+                       int mem, void *stream);
+
+/*
+ * pimpc_linearise -- linearise(xbar, ubar): explicit-Euler linearisation of a built-in model
+ * along a trajectory (the real-time-iteration scheme the paper's NMPC uses, Sec. I and Sec. V-C):
+ *   A_k = I + dt df/dx, B_k = dt df/du, e_k = F(xbar_k, ubar_k) - A_k xbar_k - B_k ubar_k,
+ *   F(x, u) = x + dt f(x, u), evaluated at (xbar_k, ubar_k), k = 0..N-1.
+ *   model   PIMPC_MODEL_*; every instance must have that model's (nx, nu).
+ *   params  [batch][P] model parameters (quadrotor P = 7: m, g, Jx, Jy, Jz, l, k_yaw;
+ *           cart-pole P = 4: m_cart, m_pole, half-length, g; CSTR P = 4: C_Ai, k0, EaR, T_i).
+ *   xbar [sum N nx], ubar [sum N nu]  linearisation points (lti = 1: [sum nx], [sum nu]).
+ *   dt > 0.
+ * Replaces the dynamics and marks the factorisation stale. Errors: PIMPC_EINVAL.
+ */
+int pimpc_linearise(pimpc_solver *s, int model, const double *params, double dt,
+                    const double *xbar, const double *ubar, int mem, void *stream);
+
+/*
+ * pimpc_get_dynamics -- copy out the stage matrices in use (as set by pimpc_set_dynamics or
+ * produced by pimpc_linearise), FP64, in the layout of pimpc_set_dynamics. Any pointer may be NULL.
+ */
+int pimpc_get_dynamics(pimpc_solver *s, double *A, double *B, double *e, int mem, void *stream);
+
+/*
+ * pimpc_factorise -- the per-stage cache of Algorithm 1 in FP64: for every stage,
+ *   H_k = (Qbar + rho I + rho Abar_{k+1}^T Abar_{k+1})^{-1} (k < N-1), H_{N-1} = (Qbar + rho I)^{-1}
+ *   (definition after the velocity-form iteration) and M_k = (B_k^T B_k + I + Wdu / rho)^{-1},
+ *   so that J_k v = M_k Bbar_k^T v, by Cholesky factorisation. Results are stored in the
+ *   iteration precision. pimpc_solve calls it implicitly when the cache is stale.
+ * Errors: PIMPC_ECUDA.
+ */
+int pimpc_factorise(pimpc_solver *s, void *stream);
+
+/*
+ * pimpc_solve -- solve(x0, ref, iters | tol): Algorithm 1 on every instance.
+ *   x0 [sum nx]          measured state x(t).
+ *   u_prev [sum nu]      u(t-1) in xbar_0 = (x(t), u(t-1)); NULL = 0 (Algorithm 1 input).
+ *   ref                  reference of xbar_{k+1} = (x_{k+1}, u_k): [sum N n] if ref_per_stage,
+ *                        else [sum n]; qbar_k = Qbar ref_k. NULL = 0.
+ *   warm_start           0: cold start (all iterates 0); 1: start from the iterates the previous
+ *                        solve left (Algorithm 1 output); 2: the same, shifted one stage earlier
+ *                        with the last stage repeated.
+ *   u_out [sum N nu], x_out [sum N nx]   u_k and x_{k+1} read from z_{k+1} (inside the box);
+ *                        either may be NULL.
+ *   iters[batch], c[batch], status[batch]  iterations run, last c^{i+1}, PIMPC_CONVERGED /
+ *                        MAXITER / NONFINITE; any may be NULL.
+ * Errors: PIMPC_EINVAL, PIMPC_ECUDA.
+ */
+int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const double *ref,
+                int ref_per_stage, int warm_start, double *u_out, double *x_out, int *iters,
+                double *c, int *status, int mem, void *stream);
+
+/*
+ * pimpc_get_iterates -- copy the iterates the last solve ended with (the non-hat iterates that
+ * Algorithm 1 outputs for warm start): z, v, theta, beta, lambda, each [sum N n], with
+ * z[k] = z_{k+1}, v[k] = v_k, theta[k] = theta_k, ... Any pointer may be NULL.
+ * Errors: PIMPC_ESTATE before the first solve.
+ */
+int pimpc_get_iterates(pimpc_solver *s, double *z, double *v, double *theta, double *beta,
+                       double *lambda, int mem, void *stream);
+
+/*
+ * pimpc_get_stats -- per-instance results of the last solve: iters[batch], c[batch] (last
+ * c^{i+1}), status[batch], momentum_iters[batch] (iterations whose hats used the momentum step
+ * of Algorithm 1 step 6, i.e. read the iterate before the current one). Any pointer may be NULL.
+ * Errors: PIMPC_ESTATE before the first solve.
+ */
+int pimpc_get_stats(pimpc_solver *s, int *iters, double *c, int *status, int *momentum_iters,
+                    int mem, void *stream);
+
+/*
+ * pimpc_set_restart_mask -- replay fixed restart decisions (testing aid): mask[batch][len],
+ * 1 = momentum step, 0 = restart, used for iteration i < len instead of c^{i+1} <= eta c^i;
+ * NULL clears it. Errors: PIMPC_EINVAL (len < 0 or len > max_iters).
+ */
+int pimpc_set_restart_mask(pimpc_solver *s, const unsigned char *mask, int len, int mem,
+                           void *stream);
+
+/*
+ * pimpc_plant_step -- one explicit-Euler step x_next = x + dt f(x, u) of a built-in model per
+ * instance (the closed-loop plant of the real-time-iteration loop).
+ *   params [batch][P], x [sum nx], u [sum nu], x_next [sum nx].
+ * Errors: PIMPC_EINVAL.
+ */
+int pimpc_plant_step(pimpc_solver *s, int model, const double *params, double dt,
+                     const double *x, const double *u, double *x_next, int mem, void *stream);
+
+/*
+ * pimpc_backward -- reverse mode of the unrolled iteration (an extension the paper names as
+ * future work, Sec. VI): given the loss gradients w.r.t. the outputs of the last pimpc_solve,
+ * returns the gradients w.r.t. its inputs. The last solve must have used warm_start = 0,
+ * accel = 0 and eps < 0 (a fixed number of iterations, so that the map is the unrolled one).
+ *   dL_du [sum N nu], dL_dx [sum N nx]   gradients w.r.t. u_out, x_out.
+ *   g_x0 [sum nx], g_ref [sum N n] (per-stage reference) or [sum n] (constant reference,
+ *   following the ref_per_stage of the last solve), g_q [sum nx], g_r [sum nu],
+ *   g_xmin, g_xmax [sum nx], g_umin, g_umax [sum nu]; any may be NULL.
+ *   checkpoint_every  forward states kept every K iterations (K >= 1); the other iterations
+ *                     are recomputed segment by segment.
+ * Errors: PIMPC_ESTATE (no suitable solve), PIMPC_EINVAL, PIMPC_ENOMEM (checkpoint store),
+ * PIMPC_ECUDA.
+ */
+int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, double *g_x0,
+                   double *g_ref, double *g_q, double *g_r, double *g_xmin, double *g_xmax,
+                   double *g_umin, double *g_umax, int checkpoint_every, int mem, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIMPC_H */

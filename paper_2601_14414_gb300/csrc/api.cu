@@ -1,0 +1,576 @@
+// api.cu -- the C ABI declared in include/pimpc.h: solver object, validation, host/device
+// marshalling and the launch sequence of each call. Every piece of arithmetic runs in the
+// kernels of factorise.cu, admm.cu, models.cu, adjoint.cu and misc.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "pimpc.h"
+
+using namespace pimpc;
+
+namespace pimpc {
+cudaError_t launch_unpack_state(const InstState *st, int batch, int *iters, double *c,
+                                int *status, int *momentum, cudaStream_t stream);
+cudaError_t launch_fill(double *dst, int64_t count, double value, cudaStream_t stream);
+}  // namespace pimpc
+
+namespace {
+thread_local std::string g_create_error;
+}
+
+struct pimpc_solver {
+  int device = 0, batch = 0, lti = 0, prec = 0;
+  std::vector<int> nx, nu, N, W;
+  std::vector<int64_t> off_nx, off_nu, off_n, Nnx, Nnu, Nn, offA, offB, offe, blk, stage0, bbase;
+  int64_t tot_nx = 0, tot_nu = 0, tot_n = 0, tot_Nnx = 0, tot_Nnu = 0, tot_Nn = 0;
+  int64_t tot_A = 0, tot_B = 0, tot_e = 0, tot_blk = 0, nblocks = 0, stage_words = 0;
+  int max_nx = 0, max_n = 0;
+  Layout L{};
+  std::vector<void *> allocs;
+  // device buffers
+  double *A64 = nullptr, *B64 = nullptr, *e64 = nullptr;
+  double *qd64 = nullptr, *rdu64 = nullptr, *stage64 = nullptr;
+  double *out_u = nullptr, *out_x = nullptr;
+  void *blk_T = nullptr, *it0 = nullptr, *it1 = nullptr, *qd_T = nullptr, *ref_T = nullptr;
+  void *lo_T = nullptr, *hi_T = nullptr, *xb0_T = nullptr;
+  int *cur = nullptr, *order = nullptr, *counter = nullptr, *binst = nullptr, *ferr = nullptr;
+  int64_t *d_bbase = nullptr;
+  InstState *st = nullptr;
+  unsigned char *mask = nullptr, *mask_alloc = nullptr;
+  int mask_len = 0;
+  // options and state
+  double rho = 1.0, eps = 1e-6, eta = 0.999;
+  int max_iters = 1000, accel = 1;
+  bool stale = true, have_rdu = false, solved = false;
+  int last_ref_per_stage = 0, last_warm = 0, last_accel = 0, last_iters_fixed = 0;
+  double last_eps = 0.0;
+  size_t smem_admm = 0;
+  int grid_admm = 0;
+  std::string err;
+  // adjoint workspace (allocated by the first pimpc_backward)
+  void *adj_ws = nullptr;
+  size_t adj_ws_bytes = 0;
+};
+
+namespace {
+
+int fail(pimpc_solver *s, int code, const std::string &msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+int cuda_fail(pimpc_solver *s, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(s, PIMPC_ECUDA, m);
+}
+
+#define PIMPC_CHECK(s, expr, what)                  \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return cuda_fail((s), _e, (what)); \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(pimpc_solver *s, P **p, size_t bytes) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(q);
+  *p = (P *)q;
+  return cudaSuccess;
+}
+
+size_t tsize(int prec) { return prec == PIMPC_F32 ? 4 : 8; }
+
+// Device view of a caller array: the pointer itself for device memory, else a copy in the
+// staging buffer at element offset `at`.
+cudaError_t dev_in(pimpc_solver *s, const double *p, int64_t count, int mem, int64_t at,
+                   cudaStream_t st, const double **out) {
+  if (!p) { *out = nullptr; return cudaSuccess; }
+  if (mem == PIMPC_DEVICE) { *out = p; return cudaSuccess; }
+  double *dst = s->stage64 + at;
+  cudaError_t e = cudaMemcpyAsync(dst, p, sizeof(double) * count, cudaMemcpyHostToDevice, st);
+  *out = dst;
+  return e;
+}
+
+bool finite_or_inf_ok(const double *p, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (std::isnan(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pimpc_last_error(const pimpc_solver *s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+void pimpc_destroy(pimpc_solver *s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  for (void *p : s->allocs) cudaFree(p);
+  if (s->adj_ws) cudaFree(s->adj_ws);
+  if (s->mask_alloc) cudaFree(s->mask_alloc);
+  delete s;
+}
+
+int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti, int precision,
+                 int device, pimpc_solver **out) {
+  if (!out) { g_create_error = "out is NULL"; return PIMPC_EINVAL; }
+  *out = nullptr;
+  if (batch < 1 || !nx || !nu || !N) { g_create_error = "batch < 1 or NULL size arrays"; return PIMPC_EINVAL; }
+  if (precision != PIMPC_F32 && precision != PIMPC_F64) { g_create_error = "bad precision"; return PIMPC_EINVAL; }
+  if (lti != 0 && lti != 1) { g_create_error = "lti must be 0 or 1"; return PIMPC_EINVAL; }
+  const int nmax = lti ? PIMPC_MAX_N_LTI : PIMPC_MAX_N_LTV;
+  for (int j = 0; j < batch; ++j) {
+    if (nx[j] < 1 || nu[j] < 1 || N[j] < 1 || nx[j] + nu[j] > nmax) {
+      char b[160];
+      snprintf(b, sizeof b, "instance %d: need nx >= 1, nu >= 1, N >= 1, nx + nu <= %d (got %d, %d, %d)",
+               j, nmax, nx[j], nu[j], N[j]);
+      g_create_error = b;
+      return PIMPC_EINVAL;
+    }
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    g_create_error = "no such CUDA device";
+    return PIMPC_ECUDA;
+  }
+  cudaSetDevice(device);
+  pimpc_solver *s = new pimpc_solver();
+  s->device = device; s->batch = batch; s->lti = lti; s->prec = precision;
+  s->nx.assign(nx, nx + batch); s->nu.assign(nu, nu + batch); s->N.assign(N, N + batch);
+  auto grow = [&](std::vector<int64_t> &v, int64_t &tot, int64_t add) { v.push_back(tot); tot += add; };
+  const int threads = admm_threads(precision);
+  for (int j = 0; j < batch; ++j) {
+    const int n = nx[j] + nu[j];
+    grow(s->off_nx, s->tot_nx, nx[j]);
+    grow(s->off_nu, s->tot_nu, nu[j]);
+    grow(s->off_n, s->tot_n, n);
+    grow(s->Nnx, s->tot_Nnx, (int64_t)N[j] * nx[j]);
+    grow(s->Nnu, s->tot_Nnu, (int64_t)N[j] * nu[j]);
+    grow(s->Nn, s->tot_Nn, (int64_t)N[j] * n);
+    const int64_t reps = lti ? 1 : N[j];
+    grow(s->offA, s->tot_A, reps * nx[j] * nx[j]);
+    grow(s->offB, s->tot_B, reps * nx[j] * nu[j]);
+    grow(s->offe, s->tot_e, reps * nx[j]);
+    const int w = block_words(nx[j], nu[j]);
+    s->W.push_back(w);
+    grow(s->blk, s->tot_blk, (int64_t)blocks_per_instance(lti, N[j]) * w);
+    s->stage0.push_back(s->bbase.empty() ? 0 : s->stage0.back() + N[j - 1]);
+    grow(s->bbase, s->nblocks, blocks_per_instance(lti, N[j]));
+    s->max_nx = std::max(s->max_nx, nx[j]);
+    s->max_n = std::max(s->max_n, n);
+    s->smem_admm = std::max(s->smem_admm, admm_smem_bytes(nx[j], nu[j], lti, threads, precision));
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (s->smem_admm > (size_t)optin - 1024) {
+    g_create_error = "an instance needs more shared memory than one CTA has at this precision";
+    delete s;
+    return PIMPC_EINVAL;
+  }
+  const size_t ts = tsize(precision);
+  std::vector<int> binst(s->nblocks);
+  for (int j = 0; j < batch; ++j)
+    for (int b = 0; b < blocks_per_instance(lti, N[j]); ++b) binst[s->bbase[j] + b] = j;
+  // Work order: largest streamed volume first.
+  std::vector<int> order(batch);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> cost(batch);
+  for (int j = 0; j < batch; ++j) {
+    const int n = nx[j] + nu[j];
+    cost[j] = (double)N[j] * ((lti ? 0 : s->W[j]) + 15.0 * n);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+
+  const int64_t stage_words = std::max<int64_t>(
+      {2 * s->tot_nx + 2 * s->tot_nu, s->tot_nx + s->tot_nu + s->tot_Nn,
+       s->tot_Nnx + s->tot_Nnu + 8 * (int64_t)batch, s->tot_Nnx + s->tot_Nnu + 2 * s->tot_Nn,
+       s->tot_n + s->tot_Nn});
+  s->stage_words = stage_words;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  std::vector<int64_t *> d64;
+  int64_t *d_off[13];
+  std::vector<int64_t> *h_off[13] = {&s->off_nx, &s->off_nu, &s->off_n, &s->Nnx, &s->Nnu, &s->Nn,
+                                     &s->offA, &s->offB, &s->offe, &s->blk, &s->stage0, &s->bbase,
+                                     nullptr};
+  for (int i = 0; i < 12; ++i) {
+    chk(dalloc(s, &d_off[i], sizeof(int64_t) * batch));
+    if (e == cudaSuccess) chk(cudaMemcpy(d_off[i], h_off[i]->data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
+  }
+  int *d_nx = nullptr, *d_nu = nullptr, *d_N = nullptr, *d_W = nullptr;
+  chk(dalloc(s, &d_nx, sizeof(int) * batch));
+  chk(dalloc(s, &d_nu, sizeof(int) * batch));
+  chk(dalloc(s, &d_N, sizeof(int) * batch));
+  chk(dalloc(s, &d_W, sizeof(int) * batch));
+  if (e == cudaSuccess) {
+    chk(cudaMemcpy(d_nx, nx, sizeof(int) * batch, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(d_nu, nu, sizeof(int) * batch, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(d_N, N, sizeof(int) * batch, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(d_W, s->W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  }
+  chk(dalloc(s, &s->A64, sizeof(double) * s->tot_A));
+  chk(dalloc(s, &s->B64, sizeof(double) * s->tot_B));
+  chk(dalloc(s, &s->e64, sizeof(double) * s->tot_e));
+  chk(dalloc(s, &s->qd64, sizeof(double) * s->tot_n));
+  chk(dalloc(s, &s->rdu64, sizeof(double) * s->tot_n));
+  chk(dalloc(s, &s->stage64, sizeof(double) * stage_words));
+  chk(dalloc(s, &s->out_u, sizeof(double) * s->tot_Nnu));
+  chk(dalloc(s, &s->out_x, sizeof(double) * s->tot_Nnx));
+  chk(dalloc(s, &s->blk_T, ts * s->tot_blk));
+  chk(dalloc(s, &s->it0, ts * 5 * s->tot_Nn));
+  chk(dalloc(s, &s->it1, ts * 5 * s->tot_Nn));
+  chk(dalloc(s, &s->qd_T, ts * s->tot_n));
+  chk(dalloc(s, &s->ref_T, ts * std::max(s->tot_Nn, s->tot_n)));
+  chk(dalloc(s, &s->lo_T, ts * s->tot_n));
+  chk(dalloc(s, &s->hi_T, ts * s->tot_n));
+  chk(dalloc(s, &s->xb0_T, ts * s->tot_n));
+  chk(dalloc(s, &s->cur, sizeof(int) * batch));
+  chk(dalloc(s, &s->order, sizeof(int) * batch));
+  chk(dalloc(s, &s->counter, sizeof(int) * 4));
+  chk(dalloc(s, &s->binst, sizeof(int) * s->nblocks));
+  chk(dalloc(s, &s->ferr, sizeof(int) * 4));
+  chk(dalloc(s, &s->st, sizeof(InstState) * batch));
+  if (e != cudaSuccess) {
+    g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
+    pimpc_destroy(s);
+    return e == cudaErrorMemoryAllocation ? PIMPC_ENOMEM : PIMPC_ECUDA;
+  }
+  s->d_bbase = d_off[11];
+  chk(cudaMemcpy(s->order, order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->binst, binst.data(), sizeof(int) * s->nblocks, cudaMemcpyHostToDevice));
+  chk(cudaMemset(s->A64, 0, sizeof(double) * s->tot_A));
+  chk(cudaMemset(s->B64, 0, sizeof(double) * s->tot_B));
+  chk(cudaMemset(s->e64, 0, sizeof(double) * s->tot_e));
+  chk(cudaMemset(s->qd64, 0, sizeof(double) * s->tot_n));
+  chk(cudaMemset(s->rdu64, 0, sizeof(double) * s->tot_n));
+  chk(cudaMemset(s->qd_T, 0, ts * s->tot_n));
+  chk(cudaMemset(s->it0, 0, ts * 5 * s->tot_Nn));
+  chk(cudaMemset(s->it1, 0, ts * 5 * s->tot_Nn));
+  chk(cudaMemset(s->cur, 0, sizeof(int) * batch));
+  chk(cudaMemset(s->ferr, 0, sizeof(int) * 4));
+  chk(cudaMemset(s->st, 0, sizeof(InstState) * batch));
+  // Infinite bounds by default.
+  {
+    std::vector<double> inf(s->tot_n, INFINITY);
+    chk(cudaMemcpy(s->stage64, inf.data(), sizeof(double) * s->tot_n, cudaMemcpyHostToDevice));
+    chk(launch_convert(s->stage64, s->tot_n, precision, s->hi_T, 0));
+    for (auto &v : inf) v = -INFINITY;
+    chk(cudaMemcpy(s->stage64, inf.data(), sizeof(double) * s->tot_n, cudaMemcpyHostToDevice));
+    chk(launch_convert(s->stage64, s->tot_n, precision, s->lo_T, 0));
+    chk(cudaDeviceSynchronize());
+  }
+  Layout &L = s->L;
+  L.batch = batch; L.lti = lti; L.nx = d_nx; L.nu = d_nu; L.N = d_N;
+  L.off_nx = d_off[0]; L.off_nu = d_off[1]; L.off_n = d_off[2];
+  L.Nnx = d_off[3]; L.Nnu = d_off[4]; L.Nn = d_off[5];
+  L.offA = d_off[6]; L.offB = d_off[7]; L.offe = d_off[8];
+  L.blk = d_off[9]; L.W = d_W; L.stage0 = d_off[10];
+  int bps = 0, nsm = 0;
+  chk(admm_configure(precision, s->smem_admm, &bps));
+  chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+  if (e != cudaSuccess || bps < 1) {
+    g_create_error = std::string("kernel configuration failed: ") +
+                     (e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy");
+    pimpc_destroy(s);
+    return PIMPC_ECUDA;
+  }
+  s->grid_admm = std::min(batch, bps * nsm);
+  *out = s;
+  return PIMPC_OK;
+}
+
+int pimpc_set_options(pimpc_solver *s, double rho, double eps, int max_iters, int accel,
+                      double eta) {
+  if (!s) return PIMPC_EINVAL;
+  if (!(rho > 0.0) || !std::isfinite(rho)) return fail(s, PIMPC_EINVAL, "rho must be > 0");
+  if (std::isnan(eps)) return fail(s, PIMPC_EINVAL, "eps is NaN");
+  if (max_iters < 0) return fail(s, PIMPC_EINVAL, "max_iters < 0");
+  if (accel != 0 && accel != 1) return fail(s, PIMPC_EINVAL, "accel must be 0 or 1");
+  if (!(eta >= 0.0) || !std::isfinite(eta)) return fail(s, PIMPC_EINVAL, "eta must be >= 0");
+  if (s->mask && s->mask_len > max_iters) return fail(s, PIMPC_EINVAL, "restart mask longer than max_iters");
+  if (rho != s->rho) s->stale = true;
+  s->rho = rho; s->eps = eps; s->max_iters = max_iters; s->accel = accel; s->eta = eta;
+  return PIMPC_OK;
+}
+
+int pimpc_set_weights(pimpc_solver *s, const double *q, const double *r, const double *rdu,
+                      int mem, void *stream) {
+  if (!s || !q || !r) return fail(s, PIMPC_EINVAL, "q and r are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  if (mem == PIMPC_HOST) {
+    for (int64_t i = 0; i < s->tot_nx; ++i)
+      if (!(q[i] >= 0.0) || !std::isfinite(q[i])) return fail(s, PIMPC_EINVAL, "q must be finite and >= 0");
+    for (int64_t i = 0; i < s->tot_nu; ++i) {
+      if (!(r[i] >= 0.0) || !std::isfinite(r[i])) return fail(s, PIMPC_EINVAL, "r must be finite and >= 0");
+      if (rdu && (!(rdu[i] >= 0.0) || !std::isfinite(rdu[i])))
+        return fail(s, PIMPC_EINVAL, "rdu must be finite and >= 0");
+    }
+  }
+  const double *dq, *dr, *drdu;
+  PIMPC_CHECK(s, dev_in(s, q, s->tot_nx, mem, 0, st, &dq), "copy q");
+  PIMPC_CHECK(s, dev_in(s, r, s->tot_nu, mem, s->tot_nx, st, &dr), "copy r");
+  PIMPC_CHECK(s, dev_in(s, rdu, s->tot_nu, mem, s->tot_nx + s->tot_nu, st, &drdu), "copy rdu");
+  PIMPC_CHECK(s, launch_gather_n64(s->L, dq, dr, s->tot_n, s->qd64, st), "weights");
+  PIMPC_CHECK(s, launch_gather_n(s->L, dq, dr, s->tot_n, s->prec, s->qd_T, st), "weights");
+  PIMPC_CHECK(s, launch_gather_n64(s->L, nullptr, drdu, s->tot_n, s->rdu64, st), "weights");
+  s->have_rdu = rdu != nullptr;
+  s->stale = true;
+  if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "set_weights");
+  return PIMPC_OK;
+}
+
+int pimpc_set_bounds(pimpc_solver *s, const double *xmin, const double *xmax, const double *umin,
+                     const double *umax, int mem, void *stream) {
+  if (!s || !xmin || !xmax || !umin || !umax) return fail(s, PIMPC_EINVAL, "all four bounds are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  if (mem == PIMPC_HOST) {
+    if (!finite_or_inf_ok(xmin, s->tot_nx) || !finite_or_inf_ok(xmax, s->tot_nx) ||
+        !finite_or_inf_ok(umin, s->tot_nu) || !finite_or_inf_ok(umax, s->tot_nu))
+      return fail(s, PIMPC_EINVAL, "NaN bound");
+    for (int64_t i = 0; i < s->tot_nx; ++i)
+      if (xmin[i] > xmax[i]) return fail(s, PIMPC_EINVAL, "xmin > xmax");
+    for (int64_t i = 0; i < s->tot_nu; ++i)
+      if (umin[i] > umax[i]) return fail(s, PIMPC_EINVAL, "umin > umax");
+  }
+  const double *a, *b, *c, *d;
+  int64_t o = 0;
+  PIMPC_CHECK(s, dev_in(s, xmin, s->tot_nx, mem, o, st, &a), "copy bounds"); o += s->tot_nx;
+  PIMPC_CHECK(s, dev_in(s, xmax, s->tot_nx, mem, o, st, &b), "copy bounds"); o += s->tot_nx;
+  PIMPC_CHECK(s, dev_in(s, umin, s->tot_nu, mem, o, st, &c), "copy bounds"); o += s->tot_nu;
+  PIMPC_CHECK(s, dev_in(s, umax, s->tot_nu, mem, o, st, &d), "copy bounds");
+  PIMPC_CHECK(s, launch_gather_n(s->L, a, c, s->tot_n, s->prec, s->lo_T, st), "bounds");
+  PIMPC_CHECK(s, launch_gather_n(s->L, b, d, s->tot_n, s->prec, s->hi_T, st), "bounds");
+  if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "set_bounds");
+  return PIMPC_OK;
+}
+
+int pimpc_set_dynamics(pimpc_solver *s, const double *A, const double *B, const double *e,
+                       int mem, void *stream) {
+  if (!s || !A || !B) return fail(s, PIMPC_EINVAL, "A and B are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  const cudaMemcpyKind kind = mem == PIMPC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  PIMPC_CHECK(s, cudaMemcpyAsync(s->A64, A, sizeof(double) * s->tot_A, kind, st), "copy A");
+  PIMPC_CHECK(s, cudaMemcpyAsync(s->B64, B, sizeof(double) * s->tot_B, kind, st), "copy B");
+  if (e) PIMPC_CHECK(s, cudaMemcpyAsync(s->e64, e, sizeof(double) * s->tot_e, kind, st), "copy e");
+  else PIMPC_CHECK(s, cudaMemsetAsync(s->e64, 0, sizeof(double) * s->tot_e, st), "zero e");
+  s->stale = true;
+  if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "set_dynamics");
+  return PIMPC_OK;
+}
+
+int pimpc_linearise(pimpc_solver *s, int model, const double *params, double dt,
+                    const double *xbar, const double *ubar, int mem, void *stream) {
+  if (!s || !params || !xbar || !ubar) return fail(s, PIMPC_EINVAL, "params, xbar and ubar are required");
+  int mnx, mnu;
+  if (model_dims(model, &mnx, &mnu)) return fail(s, PIMPC_EINVAL, "unknown model");
+  for (int j = 0; j < s->batch; ++j)
+    if (s->nx[j] != mnx || s->nu[j] != mnu) return fail(s, PIMPC_EINVAL, "instance sizes do not match the model");
+  if (!(dt > 0.0)) return fail(s, PIMPC_EINVAL, "dt must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  const int64_t npts = s->lti ? s->batch : s->nblocks;
+  const int64_t nxp = s->lti ? s->tot_nx : s->tot_Nnx, nup = s->lti ? s->tot_nu : s->tot_Nnu;
+  const double *dx, *du, *dp;
+  PIMPC_CHECK(s, dev_in(s, xbar, nxp, mem, 0, st, &dx), "copy xbar");
+  PIMPC_CHECK(s, dev_in(s, ubar, nup, mem, nxp, st, &du), "copy ubar");
+  PIMPC_CHECK(s, dev_in(s, params, (int64_t)s->batch * model_nparams(model), mem, nxp + nup, st, &dp), "copy params");
+  PIMPC_CHECK(s, launch_linearise(s->L, model, dp, dt, dx, du, s->A64, s->B64, s->e64, npts,
+                                  s->lti ? nullptr : s->binst, s->lti ? nullptr : s->d_bbase, st),
+              "linearise");
+  s->stale = true;
+  if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "linearise");
+  return PIMPC_OK;
+}
+
+int pimpc_get_dynamics(pimpc_solver *s, double *A, double *B, double *e, int mem, void *stream) {
+  if (!s) return PIMPC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  const cudaMemcpyKind kind = mem == PIMPC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (A) PIMPC_CHECK(s, cudaMemcpyAsync(A, s->A64, sizeof(double) * s->tot_A, kind, st), "copy A");
+  if (B) PIMPC_CHECK(s, cudaMemcpyAsync(B, s->B64, sizeof(double) * s->tot_B, kind, st), "copy B");
+  if (e) PIMPC_CHECK(s, cudaMemcpyAsync(e, s->e64, sizeof(double) * s->tot_e, kind, st), "copy e");
+  if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "get_dynamics");
+  return PIMPC_OK;
+}
+
+int pimpc_factorise(pimpc_solver *s, void *stream) {
+  if (!s) return PIMPC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  PIMPC_CHECK(s, launch_factorise(s->L, s->A64, s->B64, s->e64, s->qd64,
+                                  s->have_rdu ? s->rdu64 : nullptr, s->rho, s->binst, s->d_bbase,
+                                  s->nblocks, s->max_nx, s->max_n, s->prec, s->blk_T, s->ferr, st),
+              "factorise");
+  s->stale = false;
+  return PIMPC_OK;
+}
+
+int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const double *ref,
+                int ref_per_stage, int warm_start, double *u_out, double *x_out, int *iters,
+                double *c, int *status, int mem, void *stream) {
+  if (!s || !x0) return fail(s, PIMPC_EINVAL, "x0 is required");
+  if (warm_start < 0 || warm_start > 2) return fail(s, PIMPC_EINVAL, "warm_start must be 0, 1 or 2");
+  if (ref_per_stage != 0 && ref_per_stage != 1) return fail(s, PIMPC_EINVAL, "ref_per_stage must be 0 or 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  if (s->stale) {
+    int rc = pimpc_factorise(s, stream);
+    if (rc) return rc;
+  }
+  const double *dx0, *dup, *dref;
+  const int64_t nref = ref_per_stage ? s->tot_Nn : s->tot_n;
+  PIMPC_CHECK(s, dev_in(s, x0, s->tot_nx, mem, 0, st, &dx0), "copy x0");
+  PIMPC_CHECK(s, dev_in(s, u_prev, s->tot_nu, mem, s->tot_nx, st, &dup), "copy u_prev");
+  PIMPC_CHECK(s, dev_in(s, ref, nref, mem, s->tot_nx + s->tot_nu, st, &dref), "copy ref");
+  PIMPC_CHECK(s, launch_gather_n(s->L, dx0, dup, s->tot_n, s->prec, s->xb0_T, st), "x0");
+  if (dref) PIMPC_CHECK(s, launch_convert(dref, nref, s->prec, s->ref_T, st), "ref");
+  PIMPC_CHECK(s, cudaMemsetAsync(s->counter, 0, sizeof(int), st), "reset queue");
+  AdmmLaunch a;
+  a.L = s->L; a.blk = s->blk_T; a.it0 = s->it0; a.it1 = s->it1; a.cur = s->cur;
+  a.qd = s->qd_T; a.ref = dref ? s->ref_T : nullptr; a.ref_per_stage = ref_per_stage;
+  a.lo = s->lo_T; a.hi = s->hi_T; a.xb0 = s->xb0_T;
+  a.rho = s->rho; a.eps = s->eps; a.eta = s->eta; a.max_iters = s->max_iters; a.accel = s->accel;
+  a.mask = s->mask; a.mask_len = s->mask_len; a.order = s->order; a.counter = s->counter;
+  a.st = s->st; a.warm = warm_start;
+  const bool dev = mem == PIMPC_DEVICE;
+  a.u_out = u_out ? (dev ? u_out : s->out_u) : nullptr;
+  a.x_out = x_out ? (dev ? x_out : s->out_x) : nullptr;
+  PIMPC_CHECK(s, launch_admm(a, s->prec, s->grid_admm, s->smem_admm, st), "solve");
+  s->solved = true;
+  s->last_ref_per_stage = ref_per_stage;
+  s->last_warm = warm_start;
+  s->last_accel = s->accel;
+  s->last_eps = s->eps;
+  s->last_iters_fixed = s->max_iters;
+  if (dev) {
+    if (iters || c || status)
+      PIMPC_CHECK(s, launch_unpack_state(s->st, s->batch, iters, c, status, nullptr, st), "state");
+    return PIMPC_OK;
+  }
+  if (u_out) PIMPC_CHECK(s, cudaMemcpyAsync(u_out, s->out_u, sizeof(double) * s->tot_Nnu, cudaMemcpyDeviceToHost, st), "copy u");
+  if (x_out) PIMPC_CHECK(s, cudaMemcpyAsync(x_out, s->out_x, sizeof(double) * s->tot_Nnx, cudaMemcpyDeviceToHost, st), "copy x");
+  if (iters || c || status) {
+    std::vector<InstState> hs(s->batch);
+    PIMPC_CHECK(s, cudaMemcpyAsync(hs.data(), s->st, sizeof(InstState) * s->batch, cudaMemcpyDeviceToHost, st), "copy state");
+    PIMPC_CHECK(s, cudaStreamSynchronize(st), "solve");
+    for (int j = 0; j < s->batch; ++j) {
+      if (iters) iters[j] = hs[j].iters;
+      if (c) c[j] = hs[j].c;
+      if (status) status[j] = hs[j].status;
+    }
+  } else {
+    PIMPC_CHECK(s, cudaStreamSynchronize(st), "solve");
+  }
+  return PIMPC_OK;
+}
+
+int pimpc_get_iterates(pimpc_solver *s, double *z, double *v, double *theta, double *beta,
+                       double *lambda, int mem, void *stream) {
+  if (!s) return PIMPC_EINVAL;
+  if (!s->solved) return fail(s, PIMPC_ESTATE, "no solve has run");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  double *outs[5] = {z, v, theta, beta, lambda};
+  if (mem == PIMPC_DEVICE) {
+    PIMPC_CHECK(s, launch_export_iterates(s->L, s->it0, s->it1, s->cur, s->tot_Nn, s->prec, z, v,
+                                          theta, beta, lambda, st), "export");
+    return PIMPC_OK;
+  }
+  // Host: export one array at a time through the staging buffer.
+  for (int b = 0; b < 5; ++b) {
+    if (!outs[b]) continue;
+    double *tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    tmp[b] = s->stage64;
+    PIMPC_CHECK(s, launch_export_iterates(s->L, s->it0, s->it1, s->cur, s->tot_Nn, s->prec, tmp[0],
+                                          tmp[1], tmp[2], tmp[3], tmp[4], st), "export");
+    PIMPC_CHECK(s, cudaMemcpyAsync(outs[b], s->stage64, sizeof(double) * s->tot_Nn, cudaMemcpyDeviceToHost, st), "copy iterates");
+    PIMPC_CHECK(s, cudaStreamSynchronize(st), "get_iterates");
+  }
+  return PIMPC_OK;
+}
+
+int pimpc_get_stats(pimpc_solver *s, int *iters, double *c, int *status, int *momentum_iters,
+                    int mem, void *stream) {
+  if (!s) return PIMPC_EINVAL;
+  if (!s->solved) return fail(s, PIMPC_ESTATE, "no solve has run");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  if (mem == PIMPC_DEVICE) {
+    PIMPC_CHECK(s, launch_unpack_state(s->st, s->batch, iters, c, status, momentum_iters, st), "stats");
+    return PIMPC_OK;
+  }
+  std::vector<InstState> hs(s->batch);
+  PIMPC_CHECK(s, cudaMemcpyAsync(hs.data(), s->st, sizeof(InstState) * s->batch, cudaMemcpyDeviceToHost, st), "copy stats");
+  PIMPC_CHECK(s, cudaStreamSynchronize(st), "get_stats");
+  for (int j = 0; j < s->batch; ++j) {
+    if (iters) iters[j] = hs[j].iters;
+    if (c) c[j] = hs[j].c;
+    if (status) status[j] = hs[j].status;
+    if (momentum_iters) momentum_iters[j] = hs[j].momentum;
+  }
+  return PIMPC_OK;
+}
+
+int pimpc_set_restart_mask(pimpc_solver *s, const unsigned char *mask, int len, int mem,
+                           void *stream) {
+  if (!s) return PIMPC_EINVAL;
+  cudaSetDevice(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!mask) { s->mask_len = 0; s->mask = nullptr; return PIMPC_OK; }
+  if (len < 0 || len > s->max_iters) return fail(s, PIMPC_EINVAL, "mask length must be in [0, max_iters]");
+  // Testing aid: the mask buffer is (re)allocated here, sized for this mask.
+  const size_t bytes = (size_t)s->batch * (size_t)std::max(len, 1);
+  if (s->mask_alloc) { cudaFree(s->mask_alloc); s->mask_alloc = nullptr; }
+  unsigned char *buf = nullptr;
+  PIMPC_CHECK(s, cudaMalloc((void **)&buf, bytes), "mask allocation");
+  s->mask_alloc = buf;
+  const cudaMemcpyKind kind = mem == PIMPC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  PIMPC_CHECK(s, cudaMemcpyAsync(buf, mask, (size_t)s->batch * len, kind, st), "copy mask");
+  if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "mask");
+  s->mask = buf;
+  s->mask_len = len;
+  return PIMPC_OK;
+}
+
+int pimpc_plant_step(pimpc_solver *s, int model, const double *params, double dt,
+                     const double *x, const double *u, double *x_next, int mem, void *stream) {
+  if (!s || !params || !x || !u || !x_next) return fail(s, PIMPC_EINVAL, "missing argument");
+  int mnx, mnu;
+  if (model_dims(model, &mnx, &mnu)) return fail(s, PIMPC_EINVAL, "unknown model");
+  for (int j = 0; j < s->batch; ++j)
+    if (s->nx[j] != mnx || s->nu[j] != mnu) return fail(s, PIMPC_EINVAL, "instance sizes do not match the model");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  const double *dx, *du, *dp;
+  int64_t o = 0;
+  PIMPC_CHECK(s, dev_in(s, x, s->tot_nx, mem, o, st, &dx), "copy x"); o += s->tot_nx;
+  PIMPC_CHECK(s, dev_in(s, u, s->tot_nu, mem, o, st, &du), "copy u"); o += s->tot_nu;
+  PIMPC_CHECK(s, dev_in(s, params, (int64_t)s->batch * model_nparams(model), mem, o, st, &dp), "copy params");
+  o += (int64_t)s->batch * model_nparams(model);
+  double *dxn = mem == PIMPC_DEVICE ? x_next : s->stage64 + o;
+  PIMPC_CHECK(s, launch_plant_step(s->L, model, dp, dt, dx, du, dxn, st), "plant step");
+  if (mem == PIMPC_HOST) {
+    PIMPC_CHECK(s, cudaMemcpyAsync(x_next, dxn, sizeof(double) * s->tot_nx, cudaMemcpyDeviceToHost, st), "copy x_next");
+    PIMPC_CHECK(s, cudaStreamSynchronize(st), "plant step");
+  }
+  return PIMPC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// factorise.cu -- the per-stage cache of Algorithm 1 ("cache J_k and H_k"), computed in FP64.
+//
+// For stage k (LTV) the warp forms
+//   K = Qbar + rho I + rho Abar_{k+1}^T Abar_{k+1}   (k < N-1),   K = Qbar + rho I   (k = N-1),
+// where Abar^T Abar = G^T G + diag(0, I_nu) with G = [A | B] (Theorem 2's velocity form), factors
+// K = L L^T (Cholesky) and writes H_k = K^{-1}, obtained column by column from L y = e_c and
+// L^T x = y. It also writes M_k = (B_k^T B_k + I + Wdu / rho)^{-1}, so that the du update of
+// Algorithm 1 step 1, J_k (v - beta) with J_k = (Bbar^T Bbar)^{-1} Bbar^T, is
+// M_k (B_k^T (v - beta)_x + (v - beta)_u); and it copies G_k and e_k into the stage block.
+// Outputs are converted to the iteration precision T. LTI instances have two blocks: block 0
+// with H = (Qbar + rho I + rho Abar^T Abar)^{-1} and block 1 with the terminal H_{N-1}.
+#include "launch.h"
+
+namespace pimpc {
+
+namespace {
+
+struct FactArgs {
+  Layout L;
+  const double *A, *B, *e;   // FP64 dynamics, user layout
+  const double *qd;          // [sum n] Qbar diagonal in FP64
+  const double *rdu;         // [sum n] with the W_du diagonal at the input slots (or null)
+  double rho;
+  const int *binst;          // instance of each global block
+  const int64_t *bbase;      // first global block of each instance
+  int64_t nblocks;
+  int words_per_warp;        // shared-memory doubles per warp
+  int *err;                  // set to 1 on a non-positive pivot
+};
+
+// Cholesky of the m x m matrix in S (lower triangle used, leading dimension ld) in place;
+// then overwrite X (m x m, column c owned by lane c and c + 32) with S^{-1}.
+__device__ void chol_inverse(double *S, double *X, int m, int ld, int lane, int *err) {
+  for (int j = 0; j < m; ++j) {
+    __syncwarp();
+    if (lane == 0) {
+      double d = S[j * ld + j];
+      for (int p = 0; p < j; ++p) d -= S[j * ld + p] * S[j * ld + p];
+      if (!(d > 0.0)) { *err = 1; d = 1.0; }
+      S[j * ld + j] = sqrt(d);
+    }
+    __syncwarp();
+    const double ljj = S[j * ld + j];
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      double s = S[i * ld + j];
+      for (int p = 0; p < j; ++p) s -= S[i * ld + p] * S[j * ld + p];
+      S[i * ld + j] = s / ljj;
+    }
+  }
+  __syncwarp();
+  for (int c = lane; c < m; c += 32) {
+    // forward: L y = e_c  (y_i = 0 for i < c)
+    for (int i = 0; i < c; ++i) X[i * ld + c] = 0.0;
+    X[c * ld + c] = 1.0 / S[c * ld + c];
+    for (int i = c + 1; i < m; ++i) {
+      double s = 0.0;
+      for (int p = c; p < i; ++p) s += S[i * ld + p] * X[p * ld + c];
+      X[i * ld + c] = -s / S[i * ld + i];
+    }
+    // backward: L^T x = y
+    for (int i = m - 1; i >= 0; --i) {
+      double s = X[i * ld + c];
+      for (int p = i + 1; p < m; ++p) s -= S[p * ld + i] * X[p * ld + c];
+      X[i * ld + c] = s / S[i * ld + i];
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void factorise_kernel(FactArgs a, T *blk) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (b >= a.nblocks) return;
+  double *sh = smem + (size_t)warp * a.words_per_warp;
+  const int j = a.binst[b];
+  const int kb = (int)(b - a.bbase[j]);
+  const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j], n = nx + nu;
+  const int ld = n;
+  double *G = sh;                    // nx x n
+  double *S = G + nx * n;            // n x n  (K, then L)
+  double *X = S + n * n;             // n x n  (inverse)
+  const bool lti = a.L.lti != 0;
+  const bool terminal = lti ? (kb == 1) : (kb == N - 1);
+  const double rho = a.rho;
+  const double *qd = a.qd + a.L.off_n[j];
+
+  // Dynamics of the stage whose Abar enters H (k+1), and of the stage itself (k).
+  const int kH = lti ? 0 : kb + 1;
+  const int kS = lti ? 0 : kb;
+  const double *A = a.A + a.L.offA[j];
+  const double *B = a.B + a.L.offB[j];
+  const double *e = a.e ? a.e + a.L.offe[j] : nullptr;
+
+  // K = Qbar + rho I (+ rho (G^T G + diag(0, I))), lower triangle.
+  if (!terminal) {
+    const double *Ak = A + (size_t)kH * nx * nx, *Bk = B + (size_t)kH * nx * nu;
+    for (int w = lane; w < nx * n; w += 32) {
+      int r = w / n, c = w - r * n;
+      G[w] = c < nx ? Ak[r * nx + c] : Bk[r * nu + (c - nx)];
+    }
+  }
+  __syncwarp();
+  for (int i = 0; i < n; ++i)
+    for (int c = lane; c <= i; c += 32) {
+      double s = 0.0;
+      if (!terminal) {
+        for (int r = 0; r < nx; ++r) s += G[r * n + i] * G[r * n + c];
+        if (i == c && i >= nx) s += 1.0;
+      }
+      s *= rho;
+      if (i == c) s += qd[i] + rho;
+      S[i * ld + c] = s;
+    }
+  chol_inverse(S, X, n, ld, lane, a.err);
+
+  const int W = a.L.W[j];
+  T *out = blk + a.L.blk[j] + (int64_t)kb * W;
+  const int oE = nx * n, oH = oE + nx, oM = oH + n * (n + 1) / 2;
+  for (int i = 0; i < n; ++i)
+    for (int c = lane; c <= i; c += 32) out[oH + i * (i + 1) / 2 + c] = (T)X[i * ld + c];
+  __syncwarp();
+
+  // Own-stage G_k, e_k and M_k = (B_k^T B_k + I + Wdu/rho)^{-1}.
+  const double *Ak = A + (size_t)kS * nx * nx, *Bk = B + (size_t)kS * nx * nu;
+  for (int w = lane; w < nx * n; w += 32) {
+    int r = w / n, c = w - r * n;
+    double g = c < nx ? Ak[r * nx + c] : Bk[r * nu + (c - nx)];
+    G[w] = g;
+    out[w] = (T)g;
+  }
+  for (int r = lane; r < nx; r += 32) out[oE + r] = (T)(e ? e[(size_t)kS * nx + r] : 0.0);
+  __syncwarp();
+  const double *rdu = a.rdu ? a.rdu + a.L.off_n[j] + nx : nullptr;
+  for (int i = 0; i < nu; ++i)
+    for (int c = lane; c <= i; c += 32) {
+      double s = 0.0;
+      for (int r = 0; r < nx; ++r) s += G[r * n + nx + i] * G[r * n + nx + c];
+      if (i == c) s += 1.0 + (rdu ? rdu[i] / rho : 0.0);
+      S[i * nu + c] = s;
+    }
+  chol_inverse(S, X, nu, nu, lane, a.err);
+  for (int i = 0; i < nu; ++i)
+    for (int c = lane; c <= i; c += 32) out[oM + i * (i + 1) / 2 + c] = (T)X[i * nu + c];
+  for (int w = oM + nu * (nu + 1) / 2 + lane; w < W; w += 32) out[w] = (T)0;
+}
+
+}  // namespace
+
+int factorise_smem_words(int max_nx, int max_n) { return max_nx * max_n + 2 * max_n * max_n; }
+
+cudaError_t launch_factorise(const Layout &L, const double *A, const double *B, const double *e,
+                             const double *qd, const double *rdu, double rho, const int *binst,
+                             const int64_t *bbase, int64_t nblocks, int max_nx, int max_n,
+                             int precision, void *blk, int *err, cudaStream_t stream) {
+  FactArgs a;
+  a.L = L; a.A = A; a.B = B; a.e = e; a.qd = qd; a.rdu = rdu; a.rho = rho;
+  a.binst = binst; a.bbase = bbase; a.nblocks = nblocks; a.err = err;
+  a.words_per_warp = factorise_smem_words(max_nx, max_n);
+  const size_t per_warp = (size_t)a.words_per_warp * sizeof(double);
+  int wpc = (int)((96 * 1024) / per_warp);
+  if (wpc < 1) wpc = 1;
+  if (wpc > 8) wpc = 8;
+  const size_t smem = per_warp * wpc;
+  const int64_t grid = (nblocks + wpc - 1) / wpc;
+  if (grid == 0) return cudaSuccess;
+  cudaError_t rc;
+  if (precision == 0) {
+    rc = cudaFuncSetAttribute(factorise_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+    if (rc != cudaSuccess) return rc;
+    factorise_kernel<float><<<(unsigned)grid, 32 * wpc, smem, stream>>>(a, (float *)blk);
+  } else {
+    rc = cudaFuncSetAttribute(factorise_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+    if (rc != cudaSuccess) return rc;
+    factorise_kernel<double><<<(unsigned)grid, 32 * wpc, smem, stream>>>(a, (double *)blk);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pimpc

@@ -1,0 +1,62 @@
+// launch.h -- host-side launchers of the library's kernels (internal to the library).
+#pragma once
+#include "pimpc_internal.cuh"
+
+namespace pimpc {
+
+int factorise_smem_words(int max_nx, int max_n);
+cudaError_t launch_factorise(const Layout &L, const double *A, const double *B, const double *e,
+                             const double *qd, const double *rdu, double rho, const int *binst,
+                             const int64_t *bbase, int64_t nblocks, int max_nx, int max_n,
+                             int precision, void *blk, int *err, cudaStream_t stream);
+
+struct AdmmLaunch {
+  Layout L;
+  const void *blk;
+  void *it0, *it1;
+  int *cur;
+  const void *qd, *ref;
+  int ref_per_stage;
+  const void *lo, *hi, *xb0;
+  double rho, eps, eta;
+  int max_iters, accel;
+  const unsigned char *mask;
+  int mask_len;
+  const int *order;
+  int *counter;
+  InstState *st;
+  double *u_out, *x_out;
+  int warm;
+};
+
+// Shared-memory bytes the ADMM kernel needs for an instance with these sizes.
+size_t admm_smem_bytes(int nx, int nu, int lti, int threads, int precision);
+int admm_threads(int precision);
+cudaError_t admm_configure(int precision, size_t smem, int *blocks_per_sm);
+cudaError_t launch_admm(const AdmmLaunch &a, int precision, int grid, size_t smem,
+                        cudaStream_t stream);
+
+// Elementwise helpers.
+cudaError_t launch_gather_n(const Layout &L, const double *xpart, const double *upart,
+                            int64_t total_n, int precision, void *dst, cudaStream_t stream);
+cudaError_t launch_gather_n64(const Layout &L, const double *xpart, const double *upart,
+                              int64_t total_n, double *dst, cudaStream_t stream);
+cudaError_t launch_convert(const double *src, int64_t count, int precision, void *dst,
+                           cudaStream_t stream);
+cudaError_t launch_export_iterates(const Layout &L, const void *it0, const void *it1,
+                                   const int *cur, int64_t total_stage_n, int precision,
+                                   double *z, double *v, double *th, double *be, double *la,
+                                   cudaStream_t stream);
+
+// Models.
+int model_nparams(int model);
+int model_dims(int model, int *nx, int *nu);
+cudaError_t launch_linearise(const Layout &L, int model, const double *params, double dt,
+                             const double *xbar, const double *ubar, double *A, double *B,
+                             double *e, int64_t total_points, const int *pinst,
+                             const int64_t *pbase, cudaStream_t stream);
+cudaError_t launch_plant_step(const Layout &L, int model, const double *params, double dt,
+                              const double *x, const double *u, double *x_next,
+                              cudaStream_t stream);
+
+}  // namespace pimpc

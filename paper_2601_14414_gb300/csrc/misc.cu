@@ -1,0 +1,128 @@
+// misc.cu -- elementwise marshalling kernels: FP64 ABI arrays <-> the solver's internal layout.
+#include "launch.h"
+
+namespace pimpc {
+
+namespace {
+
+// dst[off_n[j] + c] = c < nx ? xpart[off_nx[j] + c] : upart[off_nu[j] + c - nx]; one block per
+// instance, upart == null gives 0 for the input part.
+template <typename T>
+__global__ void gather_n_kernel(Layout L, const double *xpart, const double *upart, T *dst) {
+  const int j = blockIdx.x;
+  const int nx = L.nx[j], nu = L.nu[j], n = nx + nu;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double v;
+    if (c < nx) v = xpart ? xpart[L.off_nx[j] + c] : 0.0;
+    else v = upart ? upart[L.off_nu[j] + c - nx] : 0.0;
+    dst[L.off_n[j] + c] = (T)v;
+  }
+}
+
+template <typename T>
+__global__ void convert_kernel(const double *src, int64_t count, T *dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+// Iterates of stage k: [z | v | theta | beta | lambda] (5 n) -> five [sum N n] FP64 arrays.
+template <typename T>
+__global__ void export_kernel(Layout L, const T *it0, const T *it1, const int *cur, double *z,
+                              double *v, double *th, double *be, double *la) {
+  const int j = blockIdx.x;
+  const int n = L.nx[j] + L.nu[j], N = L.N[j];
+  const T *src = (cur[j] ? it1 : it0) + 5 * L.Nn[j];
+  double *outs[5] = {z, v, th, be, la};
+  for (int64_t t = threadIdx.x; t < (int64_t)N * n; t += blockDim.x) {
+    const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
+    for (int b = 0; b < 5; ++b)
+      if (outs[b]) outs[b][L.Nn[j] + t] = (double)src[(int64_t)k * 5 * n + b * n + c];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_n(const Layout &L, const double *xpart, const double *upart,
+                            int64_t total_n, int precision, void *dst, cudaStream_t stream) {
+  (void)total_n;
+  if (precision == 0)
+    gather_n_kernel<float><<<L.batch, 64, 0, stream>>>(L, xpart, upart, (float *)dst);
+  else
+    gather_n_kernel<double><<<L.batch, 64, 0, stream>>>(L, xpart, upart, (double *)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_n64(const Layout &L, const double *xpart, const double *upart,
+                              int64_t total_n, double *dst, cudaStream_t stream) {
+  (void)total_n;
+  gather_n_kernel<double><<<L.batch, 64, 0, stream>>>(L, xpart, upart, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const double *src, int64_t count, int precision, void *dst,
+                           cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (precision == 0)
+    convert_kernel<float><<<(unsigned)blocks, 256, 0, stream>>>(src, count, (float *)dst);
+  else
+    convert_kernel<double><<<(unsigned)blocks, 256, 0, stream>>>(src, count, (double *)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_iterates(const Layout &L, const void *it0, const void *it1,
+                                   const int *cur, int64_t total_stage_n, int precision,
+                                   double *z, double *v, double *th, double *be, double *la,
+                                   cudaStream_t stream) {
+  (void)total_stage_n;
+  if (precision == 0)
+    export_kernel<float><<<L.batch, 256, 0, stream>>>(L, (const float *)it0, (const float *)it1,
+                                                      cur, z, v, th, be, la);
+  else
+    export_kernel<double><<<L.batch, 256, 0, stream>>>(L, (const double *)it0,
+                                                       (const double *)it1, cur, z, v, th, be, la);
+  return cudaGetLastError();
+}
+
+}  // namespace pimpc
+
+namespace pimpc {
+
+namespace {
+
+__global__ void unpack_state_kernel(const InstState *st, int batch, int *iters, double *c,
+                                    int *status, int *momentum) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= batch) return;
+  if (iters) iters[j] = st[j].iters;
+  if (c) c[j] = st[j].c;
+  if (status) status[j] = st[j].status;
+  if (momentum) momentum[j] = st[j].momentum;
+}
+
+__global__ void fill_kernel(double *dst, int64_t count, double value) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = value;
+}
+
+}  // namespace
+
+cudaError_t launch_unpack_state(const InstState *st, int batch, int *iters, double *c,
+                                int *status, int *momentum, cudaStream_t stream) {
+  unpack_state_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(st, batch, iters, c, status,
+                                                               momentum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double *dst, int64_t count, double value, cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  fill_kernel<<<(unsigned)blocks, 256, 0, stream>>>(dst, count, value);
+  return cudaGetLastError();
+}
+
+}  // namespace pimpc

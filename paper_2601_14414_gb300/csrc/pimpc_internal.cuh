@@ -1,0 +1,58 @@
+// pimpc_internal.cuh -- device-side data layout shared by the library's CUDA sources.
+//
+// Batch layout. Instances are concatenated. For instance j with sizes (nx, nu, N), n = nx + nu:
+//   user-facing arrays (FP64, the C ABI): per-instance vectors at off_nx[j] / off_nu[j] / off_n[j],
+//   per-stage arrays at Nnx[j] = sum_{i<j} N_i nx_i, Nnu[j], Nn[j] = sum N_i n_i, matrices at
+//   offA[j] (sum N nx^2, or sum nx^2 when lti), offB[j], offe[j].
+//
+// Stage block (iteration precision T), the unit the ADMM kernel streams. For one stage k:
+//   [ G_k = [A_k | B_k] : nx x n row-major ][ e_k : nx ][ H_k : packed lower, n(n+1)/2 ]
+//   [ M_k : packed lower, nu(nu+1)/2 ], padded to a multiple of 4 elements (W words).
+// Packed lower row-major: element (i, j), j <= i, at i(i+1)/2 + j. An LTV instance has N blocks at
+// blk[j] + k W; an LTI instance has two: block 0 (H = H_k, k < N-1) and block 1 (H = H_{N-1}).
+//
+// Iterates (T): two buffers it[0], it[1]; stage k of instance j holds [z | v | theta | beta |
+// lambda] (5 n values, z = z_{k+1}) at 5 Nn[j] + 5 n k. cur[j] says which buffer holds the latest
+// non-hat iterate; the other holds the one before it (used by the momentum step).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pimpc {
+
+constexpr int kConverged = 0;   // per-instance status codes (same values as the C ABI)
+constexpr int kMaxIter = 1;
+constexpr int kNonFinite = 2;
+constexpr int kMaxNLtv = 32;
+constexpr int kMaxNLti = 64;
+
+struct Layout {
+  int batch;
+  int lti;
+  const int *nx, *nu, *N;          // [batch]
+  const int64_t *off_nx, *off_nu, *off_n;   // per-instance vector offsets
+  const int64_t *Nnx, *Nnu, *Nn;   // per-stage array offsets
+  const int64_t *offA, *offB, *offe;
+  const int64_t *blk;              // stage-block offsets (elements of T)
+  const int *W;                    // stage-block size (elements)
+  const int64_t *stage0;           // global index of the instance's first stage
+};
+
+__host__ __device__ inline int packed_size(int n) { return n * (n + 1) / 2; }
+__host__ __device__ inline int block_words(int nx, int nu) {
+  int n = nx + nu;
+  int w = nx * n + nx + packed_size(n) + packed_size(nu);
+  return (w + 3) & ~3;
+}
+__host__ __device__ inline int blocks_per_instance(int lti, int N) { return lti ? 2 : N; }
+
+// Per-instance solver state kept on the device between calls.
+struct InstState {
+  int iters;      // iterations run by the last solve
+  int status;     // kConverged / kMaxIter / kNonFinite
+  int momentum;   // iterations that read the previous iterate (momentum factor != 0)
+  int pad;
+  double c;       // last c^{i+1}
+};
+
+}  // namespace pimpc
