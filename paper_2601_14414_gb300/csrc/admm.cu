@@ -1,43 +1,99 @@
-// admm.cu -- the piMPC iteration (Algorithm 1) on a batch of instances, one CTA per instance.
+// admm.cu -- the piMPC iteration (Algorithm 1) on a batch of instances in one persistent launch.
 //
-// One launch solves the whole batch: each CTA takes instances from a work queue ordered by
-// decreasing cost (N n^2) and runs Algorithm 1 on it until c^{i+1} <= eps or K_max iterations.
-// Every iteration is one sweep over the horizon in chunks of S stages. A chunk's stage blocks
-// (G_k = [A_k | B_k], e_k, packed H_k and M_k) are staged in shared memory, with H_k and M_k
-// expanded to full symmetric matrices and odd row strides so that row and column accesses are
-// free of bank conflicts; the next stage's block is loaded too because step 1 of stage k uses
-// Abar_{k+1}. Each stage is handled by a group of g lanes (g = 8, 16 or 32 >= n; lane = vector
-// component, two components per lane when n > 32).
+// Work decomposition. The stages of every instance are cut into items of consecutive stages
+// (item = instance j, stages [a, b)). One cooperative launch runs all iterations of all
+// instances in lock-step: in iteration i every CTA pulls items from a queue and runs the
+// iteration on their stages; a grid barrier separates iterations. Because Algorithm 1 is
+// parallel in the horizon (every update of stage k reads only stages k-1, k and k+1), an item
+// needs one stage of halo on each side: the block and hats of stage a-1 to recompute
+// xbar_a = H_{a-1} h_{a-1}, and G_b, e_b and the hats of stage b for h_{b-1}. The CTA that
+// finishes the last item of an instance (per-instance atomic counter) owns the reduction of
+// c^{i+1} and applies the stop test (step 5) and the momentum / restart rule (steps 6-7) for that
+// instance. Stopped instances leave the queue (stream compaction after the barrier), so the
+// remaining instances keep every SM busy and an instance that needs many iterations is spread
+// over many CTAs instead of running alone.
 //
-// Per chunk:  load -> [phase 1: step 1 of Algorithm 1: du_k = M_k (B_k^T w_x + w_u),
-//             w = vhat_k - betahat_k; h_k = qbar_k + rho (zhat_k - thetahat_k +
-//             Abar_{k+1}^T (zhat_{k+1} - vhat_{k+1} - ebar_{k+1} + lambdahat_{k+1}));
-//             xbar_{k+1} = H_k h_k]  -> barrier ->
-//             [phase 2: steps 2-3 with xbar_k from the previous stage (or xbar_0): gamma_k,
-//             z_{k+1} = Proj((2 (xbar_{k+1} + thetahat + Abar xbar_k + ebar - lambdahat) + gamma)/3),
-//             v_k = (z + gamma)/2, the three dual updates, and the step-4 terms of c]
-// The hats of Algorithm 1 are never stored: with the momentum factor f_i = (alpha_i - 1) /
-// alpha_{i+1} (0 after a restart), hat = cur + f (cur - prev) is formed when cur and prev are
-// read; the new iterate overwrites prev, and the roles of the two buffers swap. After the sweep
-// the CTA reduces c (warp shuffles, then shared memory), applies the stop test (step 5) and the
-// momentum / restart rule (steps 6-7). Every loop is bounded by K_max: nothing waits on another
-// CTA.
+// Data movement. Stage blocks (G_k = [A_k | B_k] row-major, e_k, H_k and M_k stored diagonal by
+// diagonal) and the iterates of a sub-chunk of S stages (plus the next stage) arrive in shared
+// memory by cp.async.bulk copies completing on an mbarrier, double-buffered: the copies of
+// sub-chunk s+1 are in flight while sub-chunk s is computed. Every wait is bounded; a timeout
+// raises an error flag that ends the launch (no instance is marked converged).
+//
+// Iterates. Three buffers rotate: iteration i reads cur = buf[(base + i) % 3] and, when the
+// momentum factor f_i = (alpha_i - 1) / alpha_{i+1} is nonzero, prev = buf[(base + i - 1) % 3];
+// the hats of Algorithm 1 are formed on the fly (hat = cur + f (cur - prev)) and the new
+// iterate goes to the third buffer, so neighbouring items of the same instance never read
+// what another CTA writes in the same iteration.
+//
+// Compute. A group of g lanes (8, 16 or 32 >= n; two components per lane when n > 32) handles one
+// stage. Phase 1 (step 1): du_k = M_k (B_k^T w_x + w_u), w = vhat_k - betahat_k;
+// h_k = qbar_k + rho (zhat_k - thetahat_k + Abar_{k+1}^T (zhat_{k+1} - vhat_{k+1} - ebar_{k+1} +
+// lambdahat_{k+1})); xbar_{k+1} = H_k h_k. Phase 2 (steps 2-4) with xbar_k of the previous stage:
+// gamma_k, z_{k+1} = Proj((2 (xbar_{k+1} + thetahat + Abar xbar_k + ebar - lambdahat) + gamma)/3),
+// v_k = (z + gamma) / 2, the three dual updates and the six squared norms of c.
 #include <math.h>
+
+#include <algorithm>
 
 #include "launch.h"
 
 namespace pimpc {
 
+__global__ void set_control_kernel(Ctl *c, int nitems, int batch) {
+  c->nlist[0] = nitems;
+  c->nlist[1] = 0;
+  c->active = batch;
+}
+
 namespace {
 
-constexpr int kNone = 0xFFFF;
+constexpr long long kWaitLimit = 1ll << 22;  // bounded polls of an mbarrier / the grid barrier
 
+// ---------------------------------------------------------------------------------------------
+// PTX helpers: mbarrier + bulk asynchronous copies (the non-tensor TMA form).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Orders this thread's earlier generic-proxy accesses (and those it has observed) before later
+// async-proxy (bulk copy) accesses, for both shared and global memory.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel arguments.
+// ---------------------------------------------------------------------------------------------
 template <typename T>
-struct AdmmArgs {
+struct Args {
   Layout L;
   const T *blk;
-  T *it[2];
-  int *cur;
+  T *it[3];
   const T *qd, *ref;
   int ref_per_stage;
   const T *lo, *hi, *xb0;
@@ -45,58 +101,44 @@ struct AdmmArgs {
   int max_iters, accel;
   const unsigned char *mask;
   int mask_len;
-  const int *order;
-  int *counter;
+  const int *item_inst, *item_a, *item_b;
+  int nitems;
+  const int *nitems_inst;
+  int *list[2];
+  Ctl *ctl;
+  int *base;
   InstState *st;
-  double *u_out, *x_out;
-  int warm;
+  double *alpha, *cprev, *coef, *cacc;
+  int *ndone, *stop;
+  int capI;  // elements of one iterate area (cur); prev follows at +capI
 };
 
-// Shared-memory plan of one instance (units: elements of T, then ints for the load map).
-struct Plan {
-  int n, g, S, ldg, ldh, ldm;
-  int oG, oE, oH, oM, SW;   // slot offsets and slot stride
-  int nslots;
-  int oSlots, oScr, oX, oRed, tWords;  // T-array offsets
-  int mapInts;
+__host__ __device__ inline int group_size(int n) { return n <= 8 ? 8 : (n <= 16 ? 16 : 32); }
+__host__ __device__ inline int iter_stride(int n, int tsize) {
+  const int q = 16 / tsize;  // 16-byte granules
+  return (5 * n + q - 1) / q * q;
+}
+
+// Shared-memory layout of a launch (sized by the largest instance of the batch), in elements.
+struct Smem {
+  int rawB, capB, rawI, capI, haloB, haloI, scr, X, total;
 };
 
-__host__ __device__ inline Plan make_plan(int nx, int nu, int lti, int threads) {
-  Plan p;
-  p.n = nx + nu;
-  p.g = p.n <= 8 ? 8 : (p.n <= 16 ? 16 : 32);
-  p.S = threads / p.g;
-  p.ldg = p.n | 1;
-  p.ldh = p.n | 1;
-  p.ldm = nu | 1;
-  p.oG = 0;
-  p.oE = nx * p.ldg;
-  p.oH = p.oE + nx;
-  p.oM = p.oH + p.n * p.ldh;
-  p.SW = p.oM + nu * p.ldm;
-  p.SW += (p.SW & 1);
-  p.nslots = lti ? 2 : p.S + 1;
-  p.oSlots = 0;
-  p.oScr = p.nslots * p.SW;
-  const int nv = (p.n + 1) & ~1;
-  p.oX = p.oScr + p.S * 4 * nv;
-  p.oRed = p.oX + (p.S + 1) * nv;
-  p.tWords = p.oRed + 64;
-  p.mapInts = block_words(nx, nu);
-  return p;
-}
-
-template <typename T>
-__host__ __device__ inline size_t plan_bytes(const Plan &p) {
-  return (size_t)p.tWords * sizeof(T) + (size_t)p.mapInts * sizeof(int) + 64;
-}
-
-__device__ inline int tri_row(int w) {
-  // largest i with i (i + 1) / 2 <= w
-  int i = (int)((sqrtf(8.0f * (float)w + 1.0f) - 1.0f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= w) ++i;
-  while (i * (i + 1) / 2 > w) --i;
-  return i;
+__host__ __device__ inline Smem smem_layout(int capB, int capI, int haloB, int haloI, int S_max,
+                                            int nv_max, int tsize) {
+  const int q = 16 / tsize;
+  auto up = [q](int v) { return (v + q - 1) / q * q; };
+  Smem s;
+  s.capB = up(capB);
+  s.capI = up(capI);
+  s.rawB = 0;
+  s.rawI = s.rawB + 2 * s.capB;
+  s.haloB = s.rawI + 4 * s.capI;  // two buffers x (cur, prev)
+  s.haloI = s.haloB + up(haloB);
+  s.scr = s.haloI + up(haloI);
+  s.X = s.scr + up(S_max * 4 * nv_max);
+  s.total = s.X + up((S_max + 1) * nv_max);
+  return s;
 }
 
 template <typename T>
@@ -104,194 +146,238 @@ __device__ inline T clampv(T x, T lo, T hi) {
   return x < lo ? lo : (x > hi ? hi : x);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) admm_kernel(AdmmArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sm = reinterpret_cast<T *>(smem_raw);
-  __shared__ int sInst;
-  __shared__ double sCoef;
-  __shared__ int sStop;
+// Bounded grid barrier; all CTAs of the cooperative launch are co-resident.
+__device__ bool grid_sync(Ctl *c, unsigned nblocks, int *sOk) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = &c->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      c->bar_count = 0;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      long long k = 0;
+      while (*gen == g) {
+        if (++k > kWaitLimit || *(volatile int *)&c->err) { ok = 0; break; }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (!ok) atomicExch(&c->err, 1);
+    *sOk = ok && (*(volatile int *)&c->err == 0);
+  }
+  __syncthreads();
+  return *sOk != 0;
+}
 
+// Bounded wait on an mbarrier phase (every thread polls); false and an error flag on timeout.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, Ctl *c) {
+  long long k = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++k > kWaitLimit) {
+      atomicExch(&c->err, 2);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Symmetric m x m matrix stored diagonal by diagonal: diagonal d starts at d m - d (d - 1) / 2 and
+// holds A[i][i + d], i = 0 .. m-1-d.  Returns (A x)_c; consecutive lanes read consecutive words.
+template <typename T>
+__device__ __forceinline__ T sym_diag_row(const T *D, const T *x, int m, int c) {
+  T acc0 = D[c] * x[c], acc1 = (T)0;
+  int off = m;
+  for (int d = 1; d < m; ++d) {
+    if (c + d < m) acc0 += D[off + c] * x[c + d];
+    if (c >= d) acc1 += D[off + c - d] * x[c - d];
+    off += m - d;
+  }
+  return acc0 + acc1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The persistent kernel.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int sItem, sOk;
+  __shared__ double sRed[8];
+  T *sm = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x;
   const int nthreads = blockDim.x;
+  const unsigned nblocks = gridDim.x;
+  Ctl *ctl = a.ctl;
   const int lti = a.L.lti;
 
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) sInst = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int q = sInst;
-    if (q >= a.L.batch) break;
-    const int j = a.order[q];
-    const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j];
-    const Plan P = make_plan(nx, nu, lti, nthreads);
-    const int n = P.n, g = P.g, S = P.S;
-    int *map = reinterpret_cast<int *>(sm + P.tWords);
-    T *slots = sm + P.oSlots;
-    T *X = sm + P.oX;
-    T *red = sm + P.oRed;
-    const int nv = (n + 1) & ~1;
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t par[2] = {0u, 0u};
+  bool pend[2] = {false, false};
 
-    const int W = a.L.W[j];
-    const T *blk = a.blk + a.L.blk[j];
-    const int64_t ibase = 5 * a.L.Nn[j];
-    const T *qd = a.qd + a.L.off_n[j];
-    const T *ref = a.ref ? (a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j])) : nullptr;
-    const int refstride = a.ref_per_stage ? n : 0;
-    const T *lo = a.lo + a.L.off_n[j];
-    const T *hi = a.hi + a.L.off_n[j];
-    const T *xb0 = a.xb0 + a.L.off_n[j];
-    const T rho = (T)a.rho;
-    int cur = a.cur[j];
-
-    // Load map of a stage block into the expanded slot layout.
-    for (int w = tid; w < W; w += nthreads) {
-      int d1 = kNone, d2 = kNone;
-      const int nG = nx * n, nE = nx, nH = n * (n + 1) / 2, nM = nu * (nu + 1) / 2;
-      if (w < nG) {
-        int r = w / n, c = w - r * n;
-        d1 = P.oG + r * P.ldg + c;
-      } else if (w < nG + nE) {
-        d1 = P.oE + (w - nG);
-      } else if (w < nG + nE + nH) {
-        int t = w - nG - nE;
-        int i = tri_row(t), c = t - i * (i + 1) / 2;
-        d1 = P.oH + i * P.ldh + c;
-        if (c != i) d2 = P.oH + c * P.ldh + i;
-      } else if (w < nG + nE + nH + nM) {
-        int t = w - nG - nE - nH;
-        int i = tri_row(t), c = t - i * (i + 1) / 2;
-        d1 = P.oM + i * P.ldm + c;
-        if (c != i) d2 = P.oM + c * P.ldm + i;
-      }
-      map[w] = d1 | (d2 << 16);
-    }
-    // Starting iterates: cold start zeroes the current buffer; mode 2 shifts it one stage.
-    if (a.warm == 0) {
-      T *dst = a.it[cur] + ibase;
-      for (int64_t t = tid; t < (int64_t)5 * N * n; t += nthreads) dst[t] = (T)0;
-    } else if (a.warm == 2) {
-      const T *src = a.it[cur] + ibase;
-      T *dst = a.it[cur ^ 1] + ibase;
-      for (int64_t t = tid; t < (int64_t)5 * N * n; t += nthreads) {
-        int k = (int)(t / (5 * n));
-        int r = (int)(t - (int64_t)k * 5 * n);
-        int ks = k + 1 < N ? k + 1 : N - 1;
-        dst[t] = src[(int64_t)ks * 5 * n + r];
-      }
-      cur ^= 1;
-    }
-    __syncthreads();
-    // LTI: both stage blocks (H_k and H_{N-1}) stay in shared memory for the whole solve.
-    if (lti) {
-      for (int t = tid; t < 2 * W; t += nthreads) {
-        int s = t / W, w = t - s * W;
-        int m = map[w];
-        T v = blk[t];
-        int d1 = m & 0xFFFF, d2 = (m >> 16) & 0xFFFF;
-        if (d1 != kNone) slots[s * P.SW + d1] = v;
-        if (d2 != kNone) slots[s * P.SW + d2] = v;
-      }
-    }
-
-    const int grp = tid / g;
-    const int l = tid - grp * g;
-    T *scr = sm + P.oScr + grp * 4 * nv;
-    T *sW = scr, *sY = scr + nv, *sH = scr + 2 * nv, *sDU = scr + 3 * nv;
-    const int ncl = (g == 32 && n > 32) ? 2 : 1;
-
-    double alpha = 1.0, c_prev = 1.0, coef = 0.0, c_last = 0.0;
-    int status = kMaxIter, iters = 0, nmom = 0;
-    for (int it = 0; it < a.max_iters; ++it) {
-      const T f = (T)coef;
-      nmom += coef != 0.0;
-      const bool use_prev = coef != 0.0;
-      const T *Bc = a.it[cur] + ibase;
-      const T *Bp = a.it[cur ^ 1] + ibase;
-      T *Bn = a.it[cur ^ 1] + ibase;
+  int cl = 0;
+  for (int it = 0; it < a.max_iters; ++it) {
+    const int nact = *(volatile int *)&ctl->nlist[cl];
+    bool ok = true;
+    for (;;) {
+      if (tid == 0) sItem = atomicAdd(&ctl->queue[it & 1], 1);
+      __syncthreads();
+      const int q = sItem;
+      __syncthreads();
+      if (q >= nact) break;
+      const int item = a.list[cl][q];
+      const int j = a.item_inst[item];
+      if (*(volatile int *)&a.stop[j]) continue;
+      const int ka = a.item_a[item], kb = a.item_b[item];
+      const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j], n = nx + nu;
+      const int g = group_size(n), S = nthreads / g, nv = (n + 1) & ~1;
+      const int n5p = iter_stride(n, (int)sizeof(T));
+      const int W = a.L.W[j];
+      const int bse = a.base[j];
+      const int64_t ib = a.L.Ni[j];
+      const T *Ic = a.it[(bse + it) % 3] + ib;
+      const T *Ip = a.it[(bse + it + 2) % 3] + ib;
+      T *In = a.it[(bse + it + 1) % 3] + ib;
+      const T *blk = a.blk + a.L.blk[j];
+      const double coefd = *(volatile double *)&a.coef[j];
+      const T f = (T)coefd;
+      const bool use_prev = coefd != 0.0;
+      const T rho = (T)a.rho;
+      const T *qd = a.qd + a.L.off_n[j];
+      const T *ref = a.ref ? (a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j])) : nullptr;
+      const int refstride = a.ref_per_stage ? n : 0;
+      const T *lo = a.lo + a.L.off_n[j], *hi = a.hi + a.L.off_n[j];
+      const int grp = tid / g, l = tid - grp * g;
+      const unsigned gmask = g == 32 ? 0xffffffffu : (((1u << g) - 1u) << ((tid & 31) & ~(g - 1)));
+      const int ncl = (g == 32 && n > 32) ? 2 : 1;
+      T *scr = sm + lay.scr + grp * 4 * nv;
+      T *sW = scr, *sY = scr + nv, *sH = scr + 2 * nv, *sDU = scr + 3 * nv;
+      T *X = sm + lay.X;
+      T *haloB = sm + lay.haloB, *haloI = sm + lay.haloI;
+      const T *ltiB = haloB;  // LTI: block 0 (H_k, k < N-1) then block 1 (H_{N-1})
+      const int oE = nx * n, oH = oE + nx, oM = oH + n * (n + 1) / 2;
       T cacc = (T)0;
-      for (int k0 = 0; k0 < N; k0 += S) {
-        const int cnt = min(S, N - k0);
-        // ---- load the chunk's stage blocks (plus the next stage's) ----
-        if (!lti) {
-          const int nst = cnt + (k0 + cnt < N ? 1 : 0);
-          const T *src = blk + (int64_t)k0 * W;
-          for (int t = tid; t < nst * W; t += nthreads) {
-            int s = t / W, w = t - s * W;
-            int m = map[w];
-            T v = src[t];
-            int d1 = m & 0xFFFF, d2 = (m >> 16) & 0xFFFF;
-            if (d1 != kNone) slots[s * P.SW + d1] = v;
-            if (d2 != kNone) slots[s * P.SW + d2] = v;
-          }
-        }
-        if (k0 == 0)
-          for (int c = tid; c < n; c += nthreads) X[c] = xb0[c];
-        __syncthreads();
 
-        // ---- phase 1: step 1 (du_k and xbar_{k+1}) ----
+      // Copies of the sub-chunk that starts at stage k0 into buffer b (thread 0 issues).
+      auto issue = [&](int k0, int b, bool first) {
+        const int cnt = min(S, kb - k0);
+        const int ns = cnt + ((k0 + cnt < N) ? 1 : 0);  // plus the next stage
+        const bool halo = first && ka > 0;
+        const uint32_t it_bytes = (uint32_t)(ns * n5p * sizeof(T));
+        uint32_t bytes = it_bytes * (use_prev ? 2u : 1u);
+        if (!lti) bytes += (uint32_t)(ns * W * sizeof(T));
+        if (halo) {
+          bytes += (uint32_t)(n5p * sizeof(T)) * (use_prev ? 2u : 1u);
+          if (!lti) bytes += (uint32_t)(W * sizeof(T));
+        }
+        if (lti && first) bytes += (uint32_t)(2 * W * sizeof(T));
+        fence_proxy_async();
+        mbar_expect_tx(&mbar[b], bytes);
+        T *rB = sm + lay.rawB + b * lay.capB;
+        T *rI = sm + lay.rawI + b * 2 * lay.capI;
+        if (!lti) bulk_load(rB, blk + (int64_t)k0 * W, (uint32_t)(ns * W * sizeof(T)), &mbar[b]);
+        bulk_load(rI, Ic + (int64_t)k0 * n5p, it_bytes, &mbar[b]);
+        if (use_prev) bulk_load(rI + lay.capI, Ip + (int64_t)k0 * n5p, it_bytes, &mbar[b]);
+        if (halo) {
+          if (!lti) bulk_load(haloB, blk + (int64_t)(ka - 1) * W, (uint32_t)(W * sizeof(T)), &mbar[b]);
+          bulk_load(haloI, Ic + (int64_t)(ka - 1) * n5p, (uint32_t)(n5p * sizeof(T)), &mbar[b]);
+          if (use_prev)
+            bulk_load(haloI + n5p, Ip + (int64_t)(ka - 1) * n5p, (uint32_t)(n5p * sizeof(T)), &mbar[b]);
+        }
+        if (lti && first) bulk_load(haloB, blk, (uint32_t)(2 * W * sizeof(T)), &mbar[b]);
+      };
+
+      const int nsub = (kb - ka + S - 1) / S;
+      if (tid == 0) issue(ka, 0, true);
+      pend[0] = true;
+      int b = 0;
+      for (int sc = 0; sc < nsub; ++sc, b ^= 1) {
+        const int k0 = ka + sc * S;
+        const int cnt = min(S, kb - k0);
+        if (sc + 1 < nsub) {
+          if (tid == 0) issue(k0 + S, b ^ 1, false);
+          pend[b ^ 1] = true;
+        }
+        const bool arrived = mbar_wait(&mbar[b], par[b], ctl);
+        if (!__syncthreads_and(arrived)) { ok = false; break; }  // uniform across the CTA
+        par[b] ^= 1u;
+        pend[b] = false;
+        const T *rB = sm + lay.rawB + b * lay.capB;
+        const T *rIc = sm + lay.rawI + b * 2 * lay.capI;
+        const T *rIp = rIc + lay.capI;
+
+        // ---- phase 1: step 1 ----
         T zh[2], vh[2], thh[2], beh[2], lah[2];
         const int k = k0 + grp;
         const bool active = grp < cnt;
-        const T *Sk = slots + (lti ? ((k < N - 1) ? 0 : P.SW) : grp * P.SW);
-        const T *Gk = lti ? slots : slots + grp * P.SW;         // G_k, e_k, M_k
-        const T *Gk1 = lti ? slots : slots + (grp + 1) * P.SW;  // G_{k+1}, e_{k+1}
+        const T *Hk = lti ? (ltiB + ((k < N - 1) ? 0 : W)) : rB + grp * W;  // block holding H_k
+        const T *Gk = lti ? ltiB : rB + grp * W;                           // G_k, e_k, M_k
+        const T *Gk1 = lti ? ltiB : rB + (grp + 1) * W;                    // G_{k+1}, e_{k+1}
+        const T *hc = rIc + grp * n5p, *hp = rIp + grp * n5p;
         if (active) {
-          const T *c0 = Bc + (int64_t)k * 5 * n;
-          const T *p0 = Bp + (int64_t)k * 5 * n;
           for (int qq = 0; qq < ncl; ++qq) {
             const int c = l + 32 * qq;
             if (c < n) {
-              T cz = c0[c], cv = c0[n + c], ct = c0[2 * n + c], cb = c0[3 * n + c], cl = c0[4 * n + c];
+              T cz = hc[c], cv = hc[n + c], ct = hc[2 * n + c], cb = hc[3 * n + c], cm = hc[4 * n + c];
               if (use_prev) {
-                cz += f * (cz - p0[c]);
-                cv += f * (cv - p0[n + c]);
-                ct += f * (ct - p0[2 * n + c]);
-                cb += f * (cb - p0[3 * n + c]);
-                cl += f * (cl - p0[4 * n + c]);
+                cz += f * (cz - hp[c]);
+                cv += f * (cv - hp[n + c]);
+                ct += f * (ct - hp[2 * n + c]);
+                cb += f * (cb - hp[3 * n + c]);
+                cm += f * (cm - hp[4 * n + c]);
               }
-              zh[qq] = cz; vh[qq] = cv; thh[qq] = ct; beh[qq] = cb; lah[qq] = cl;
+              zh[qq] = cz; vh[qq] = cv; thh[qq] = ct; beh[qq] = cb; lah[qq] = cm;
               sW[c] = cv - cb;
               T y = (T)0;
               if (k + 1 < N) {
-                const T *c1 = c0 + 5 * n, *p1 = p0 + 5 * n;
-                T nz = c1[c], nvv = c1[n + c], nl = c1[4 * n + c];
+                const T *nc = hc + n5p, *np = hp + n5p;
+                T nz = nc[c], nvv = nc[n + c], nl = nc[4 * n + c];
                 if (use_prev) {
-                  nz += f * (nz - p1[c]);
-                  nvv += f * (nvv - p1[n + c]);
-                  nl += f * (nl - p1[4 * n + c]);
+                  nz += f * (nz - np[c]);
+                  nvv += f * (nvv - np[n + c]);
+                  nl += f * (nl - np[4 * n + c]);
                 }
-                y = nz - nvv + nl - (c < nx ? Gk1[P.oE + c] : (T)0);
+                y = nz - nvv + nl - (c < nx ? Gk1[oE + c] : (T)0);
               }
               sY[c] = y;
             }
           }
         }
         __syncwarp();
-        if (active && l < nu) {
-          // t = B_k^T w_x + w_u
-          const int c = l;
-          T t = sW[nx + c];
-          for (int r = 0; r < nx; ++r) t += Gk[P.oG + r * P.ldg + nx + c] * sW[r];
-          sH[c] = t;
+        if (active && l < nu) {  // t = B_k^T w_x + w_u
+          T t = sW[nx + l];
+          const T *col = Gk + nx + l;
+          for (int r = 0; r < nx; ++r) t += col[r * n] * sW[r];
+          sH[l] = t;
         }
         __syncwarp();
-        if (active && l < nu) {
-          // du_k = M_k t
-          const int c = l;
-          T d = (T)0;
-          for (int cc = 0; cc < nu; ++cc) d += Gk[P.oM + cc * P.ldm + c] * sH[cc];
-          sDU[c] = d;
-        }
+        if (active && l < nu) sDU[l] = sym_diag_row(Gk + oM, sH, nu, l);  // du_k = M_k t
         __syncwarp();
         if (active) {
           for (int qq = 0; qq < ncl; ++qq) {
             const int c = l + 32 * qq;
             if (c < n) {
               T acc = (T)0;
-              if (k + 1 < N) {
-                // Abar_{k+1}^T y = G_{k+1}^T y_x + (0, y_u)
-                for (int r = 0; r < nx; ++r) acc += Gk1[P.oG + r * P.ldg + c] * sY[r];
+              if (k + 1 < N) {  // Abar_{k+1}^T y = G_{k+1}^T y_x + (0, y_u)
+                const T *col = Gk1 + c;
+                T acc1 = (T)0;
+                int r = 0;
+                for (; r + 1 < nx; r += 2) {
+                  acc += col[r * n] * sY[r];
+                  acc1 += col[(r + 1) * n] * sY[r + 1];
+                }
+                if (r < nx) acc += col[r * n] * sY[r];
+                acc += acc1;
                 if (c >= nx) acc += sY[c];
               }
               const T rf = ref ? ref[(int64_t)k * refstride + c] : (T)0;
@@ -303,10 +389,43 @@ __global__ void __launch_bounds__(256) admm_kernel(AdmmArgs<T> a) {
         if (active) {
           for (int qq = 0; qq < ncl; ++qq) {
             const int c = l + 32 * qq;
-            if (c < n) {
-              T acc = (T)0;
-              for (int cc = 0; cc < n; ++cc) acc += Sk[P.oH + cc * P.ldh + c] * sH[cc];
-              X[(grp + 1) * nv + c] = acc;
+            if (c < n) X[(grp + 1) * nv + c] = sym_diag_row(Hk + oH, sH, n, c);  // xbar_{k+1}
+          }
+        }
+        // xbar_k of the sub-chunk's first stage: xbar_0, the previous sub-chunk's last result
+        // (already in row 0), or for an item starting at a > 0, H_{a-1} h_{a-1} from the halo.
+        if (sc == 0) {
+          if (ka == 0) {
+            for (int c = tid; c < n; c += nthreads) X[c] = a.xb0[a.L.off_n[j] + c];
+          } else if (grp == 0) {
+            __syncwarp(gmask);
+            for (int qq = 0; qq < ncl; ++qq) {  // y_a from this group's own hats (stage a)
+              const int c = l + 32 * qq;
+              if (c < n) sY[c] = zh[qq] - vh[qq] + lah[qq] - (c < nx ? Gk[oE + c] : (T)0);
+            }
+            __syncwarp(gmask);
+            const T *hcm = haloI, *hpm = haloI + n5p;
+            const T *Hm = lti ? ltiB : haloB;  // a - 1 < N - 1
+            for (int qq = 0; qq < ncl; ++qq) {
+              const int c = l + 32 * qq;
+              if (c < n) {
+                const T *col = Gk + c;
+                T acc = (T)0;
+                for (int r = 0; r < nx; ++r) acc += col[r * n] * sY[r];
+                if (c >= nx) acc += sY[c];
+                T zm = hcm[c], tm = hcm[2 * n + c];
+                if (use_prev) {
+                  zm += f * (zm - hpm[c]);
+                  tm += f * (tm - hpm[2 * n + c]);
+                }
+                const T rf = ref ? ref[(int64_t)(ka - 1) * refstride + c] : (T)0;
+                sW[c] = qd[c] * rf + rho * (zm - tm + acc);
+              }
+            }
+            __syncwarp(gmask);
+            for (int qq = 0; qq < ncl; ++qq) {
+              const int c = l + 32 * qq;
+              if (c < n) X[c] = sym_diag_row(Hm + oH, sW, n, c);
             }
           }
         }
@@ -314,19 +433,32 @@ __global__ void __launch_bounds__(256) admm_kernel(AdmmArgs<T> a) {
 
         // ---- phase 2: steps 2-4 ----
         if (active) {
-          const T *xk = X + grp * nv;          // xbar_k
-          const T *xk1 = X + (grp + 1) * nv;   // xbar_{k+1}
-          T *o = Bn + (int64_t)k * 5 * n;
+          const T *xk = X + grp * nv;
+          const T *xk1 = X + (grp + 1) * nv;
+          T *o = In + (int64_t)k * n5p;
           for (int qq = 0; qq < ncl; ++qq) {
             const int c = l + 32 * qq;
             if (c < n) {
               T ax, bd, ee;
               if (c < nx) {
-                T s1 = (T)0, s2 = (T)0;
-                const T *row = Gk + P.oG + c * P.ldg;
-                for (int cc = 0; cc < n; ++cc) s1 += row[cc] * xk[cc];
-                for (int cc = 0; cc < nu; ++cc) s2 += row[nx + cc] * sDU[cc];
-                ax = s1; bd = s2; ee = Gk[P.oE + c];
+                // row c of G; the column order is rotated by c so lanes read distinct banks
+                const T *row = Gk + c * n;
+                T s1 = (T)0, s1b = (T)0, s2 = (T)0;
+                int cc = c;
+                int t = 0;
+                for (; t + 1 < n; t += 2) {
+                  s1 += row[cc] * xk[cc];
+                  cc = (cc + 1 == n) ? 0 : cc + 1;
+                  s1b += row[cc] * xk[cc];
+                  cc = (cc + 1 == n) ? 0 : cc + 1;
+                }
+                if (t < n) s1 += row[cc] * xk[cc];
+                int cu = c % nu;
+                for (int t2 = 0; t2 < nu; ++t2) {
+                  s2 += row[nx + cu] * sDU[cu];
+                  cu = (cu + 1 == nu) ? 0 : cu + 1;
+                }
+                ax = s1 + s1b; bd = s2; ee = Gk[oE + c];
               } else {
                 ax = xk[c]; bd = sDU[c - nx]; ee = (T)0;
               }
@@ -346,78 +478,234 @@ __global__ void __launch_bounds__(256) admm_kernel(AdmmArgs<T> a) {
           }
         }
         __syncthreads();
-        // xbar at the end of this chunk becomes xbar_k of the next chunk's first stage
         for (int c = tid; c < n; c += nthreads) X[c] = X[cnt * nv + c];
+        __syncthreads();
       }
-      // ---- step 4: reduce c; steps 5-7 ----
+      if (!ok) break;
+
+      // ---- step 4: this item's share of c; the last item of the instance applies steps 5-7 ----
       for (int off = 16; off > 0; off >>= 1) cacc += __shfl_xor_sync(0xffffffffu, cacc, off);
-      if ((tid & 31) == 0) red[tid >> 5] = cacc;
+      if ((tid & 31) == 0) sRed[tid >> 5] = (double)cacc;
       __syncthreads();
       if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (nthreads >> 5); ++w) s += (double)red[w];
-        const double c = (double)rho * s;
-        int stop = 0;
-        if (!isfinite(c)) {
-          status = kNonFinite; stop = 1;
-        } else if (c <= a.eps) {
-          status = kConverged; stop = 1;
-        } else {
-          int take = 0;
-          if (a.accel) {
-            if (a.mask && it < a.mask_len) take = a.mask[(int64_t)j * a.mask_len + it] != 0;
-            else take = c <= a.eta * c_prev;
-          }
-          if (take) {
-            const double an = 0.5 + 0.5 * sqrt(1.0 + 4.0 * alpha * alpha);
-            coef = (alpha - 1.0) / an;
-            alpha = an;
+        double part = 0.0;
+        for (int w = 0; w < (nthreads >> 5); ++w) part += sRed[w];
+        atomicAdd(&a.cacc[j], part);
+        __threadfence();
+        const int done = atomicAdd(&a.ndone[j], 1);
+        if (done == a.nitems_inst[j] - 1) {
+          __threadfence();
+          const double s = __longlong_as_double(
+              (long long)atomicExch((unsigned long long *)&a.cacc[j], 0ull));
+          a.ndone[j] = 0;
+          const double c = a.rho * s;
+          InstState &st = a.st[j];
+          st.iters = it + 1;
+          st.c = c;
+          int stop = 0;
+          if (!isfinite(c)) {
+            st.status = kNonFinite; stop = 1;
+          } else if (c <= a.eps) {
+            st.status = kConverged; stop = 1;
+          } else if (it + 1 >= a.max_iters) {
+            st.status = kMaxIter; stop = 1;
           } else {
-            alpha = 1.0;
-            coef = 0.0;
+            int take = 0;
+            if (a.accel) {
+              if (a.mask && it < a.mask_len) take = a.mask[(int64_t)j * a.mask_len + it] != 0;
+              else take = c <= a.eta * a.cprev[j];
+            }
+            if (take) {
+              const double al = a.alpha[j];
+              const double an = 0.5 + 0.5 * sqrt(1.0 + 4.0 * al * al);
+              a.coef[j] = (al - 1.0) / an;
+              a.alpha[j] = an;
+              if (al != 1.0) st.momentum += 1;
+            } else {
+              a.alpha[j] = 1.0;
+              a.coef[j] = 0.0;
+            }
+            a.cprev[j] = c;
           }
-          c_prev = c;
-        }
-        c_last = c;
-        sCoef = coef;
-        sStop = stop;
-      }
-      __syncthreads();
-      coef = sCoef;
-      cur ^= 1;
-      iters = it + 1;
-      if (sStop) break;
-    }
-    // Outputs: u_k and x_{k+1} from z_{k+1} of the latest iterate.
-    const T *Bf = a.it[cur] + ibase;
-    if (a.x_out || a.u_out) {
-      for (int64_t t = tid; t < (int64_t)N * n; t += nthreads) {
-        int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
-        double zval = (double)Bf[(int64_t)k * 5 * n + c];
-        if (c < nx) {
-          if (a.x_out) a.x_out[a.L.Nnx[j] + (int64_t)k * nx + c] = zval;
-        } else if (a.u_out) {
-          a.u_out[a.L.Nnu[j] + (int64_t)k * nu + (c - nx)] = zval;
+          if (stop) {
+            a.stop[j] = 1;
+            a.base[j] = (a.base[j] + it + 1) % 3;  // the buffer holding the final iterate
+            atomicSub(&ctl->active, 1);
+            atomicExch(&ctl->stopped, 1);
+          }
         }
       }
     }
-    if (tid == 0) {
-      a.cur[j] = cur;
-      a.st[j].iters = iters;
-      a.st[j].status = status;
-      a.st[j].c = c_last;
-      a.st[j].momentum = nmom;
+    if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
+    if (!grid_sync(ctl, nblocks, &sOk)) break;
+    if (*(volatile int *)&ctl->active <= 0) break;
+    // Remove the items of instances that stopped in this iteration from the queue.
+    if (*(volatile int *)&ctl->stopped) {
+      const int src = cl, dst = cl ^ 1;
+      for (int b0 = blockIdx.x * nthreads; b0 < nact; b0 += nblocks * nthreads) {
+        const int qi = b0 + tid;
+        int keep = 0, item = 0;
+        if (qi < nact) {
+          item = a.list[src][qi];
+          keep = *(volatile int *)&a.stop[a.item_inst[item]] == 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        int wbase = 0;
+        if ((tid & 31) == 0 && m) wbase = atomicAdd(&ctl->nlist[dst], __popc(m));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (keep) a.list[dst][wbase + __popc(m & ((1u << (tid & 31)) - 1u))] = item;
+      }
+      if (!grid_sync(ctl, nblocks, &sOk)) break;
+      cl = dst;
+      if (blockIdx.x == 0 && tid == 0) {
+        ctl->nlist[src] = 0;
+        ctl->stopped = 0;
+      }
+      if (!grid_sync(ctl, nblocks, &sOk)) break;
+    }
+    (void)ok;
+  }
+  // Never leave a bulk copy in flight into shared memory: wait (bounded) for pending phases.
+  for (int b = 0; b < 2; ++b)
+    if (pend[b]) {
+      long long k = 0;
+      while (!mbar_try_wait(&mbar[b], par[b]) && ++k < kWaitLimit) {
+      }
+    }
+}
+
+// One thread per instance (and per item): reset the per-instance state before a solve.
+template <typename T>
+__global__ void solve_init_kernel(Args<T> a, int warm) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.L.batch) {
+    if (warm == 2) a.base[j] = (a.base[j] + 1) % 3;  // the shifted copy is written there
+    a.alpha[j] = 1.0;
+    a.cprev[j] = 1.0;
+    a.coef[j] = 0.0;
+    a.cacc[j] = 0.0;
+    a.ndone[j] = 0;
+    a.stop[j] = a.max_iters <= 0 ? 1 : 0;
+    InstState s;
+    s.iters = 0; s.status = kMaxIter; s.momentum = 0; s.pad = 0; s.c = 0.0;
+    a.st[j] = s;
+  }
+  if (j < a.nitems) a.list[0][j] = j;
+}
+
+// Starting iterates: zero (cold start) or the previous solve's iterates shifted by one stage.
+template <typename T>
+__global__ void prepare_kernel(Args<T> a, int warm, const int *old_base) {
+  const int j = blockIdx.y;
+  const int n = a.L.nx[j] + a.L.nu[j], N = a.L.N[j];
+  const int n5p = iter_stride(n, (int)sizeof(T));
+  const int64_t ib = a.L.Ni[j];
+  T *dst = a.it[a.base[j]] + ib;
+  const T *src = a.it[old_base[j]] + ib;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n5p;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (warm == 0) {
+      dst[t] = (T)0;
+    } else {
+      const int k = (int)(t / n5p), r = (int)(t - (int64_t)k * n5p);
+      const int ks = k + 1 < N ? k + 1 : N - 1;
+      dst[t] = src[(int64_t)ks * n5p + r];
     }
   }
+}
+
+// u_k and x_{k+1} from z_{k+1} of the final iterate; instances the launch did not finish (a
+// timed-out wait) are reported as PIMPC_TIMEOUT.
+template <typename T>
+__global__ void output_kernel(Args<T> a, double *u_out, double *x_out) {
+  const int j = blockIdx.y;
+  const int nx = a.L.nx[j], nu = a.L.nu[j], n = nx + nu, N = a.L.N[j];
+  const int n5p = iter_stride(n, (int)sizeof(T));
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !a.stop[j]) a.st[j].status = kTimeout;
+  const T *z = a.it[a.base[j]] + a.L.Ni[j];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
+    const double v = (double)z[(int64_t)k * n5p + c];
+    if (c < nx) {
+      if (x_out) x_out[a.L.Nnx[j] + (int64_t)k * nx + c] = v;
+    } else if (u_out) {
+      u_out[a.L.Nnu[j] + (int64_t)k * nu + (c - nx)] = v;
+    }
+  }
+}
+
+template <typename T>
+Args<T> make_args(const AdmmLaunch &s) {
+  Args<T> a;
+  a.L = s.L;
+  a.blk = (const T *)s.blk;
+  for (int b = 0; b < 3; ++b) a.it[b] = (T *)s.it[b];
+  a.qd = (const T *)s.qd;
+  a.ref = (const T *)s.ref;
+  a.ref_per_stage = s.ref_per_stage;
+  a.lo = (const T *)s.lo;
+  a.hi = (const T *)s.hi;
+  a.xb0 = (const T *)s.xb0;
+  a.rho = s.rho; a.eps = s.eps; a.eta = s.eta;
+  a.max_iters = s.max_iters; a.accel = s.accel;
+  a.mask = s.mask; a.mask_len = s.mask_len;
+  a.item_inst = s.item_inst; a.item_a = s.item_a; a.item_b = s.item_b;
+  a.nitems = s.nitems; a.nitems_inst = s.nitems_inst;
+  a.list[0] = s.list0; a.list[1] = s.list1;
+  a.ctl = s.ctl;
+  a.base = s.base; a.st = s.st;
+  a.alpha = s.alpha; a.cprev = s.cprev; a.coef = s.coef; a.cacc = s.cacc;
+  a.ndone = s.ndone; a.stop = s.stop;
+  a.capI = 0;
+  return a;
+}
+
+template <typename T>
+Smem layout_of(const AdmmLaunch &s) {
+  return smem_layout(s.capB, s.capI, s.haloB, s.haloI, s.S_max, s.nv_max, (int)sizeof(T));
+}
+
+template <typename T>
+cudaError_t launch_t(const AdmmLaunch &s, cudaStream_t stream) {
+  Args<T> a = make_args<T>(s);
+  Smem lay = layout_of<T>(s);
+  a.capI = lay.capI;
+  cudaError_t rc = cudaMemsetAsync(s.ctl, 0, sizeof(Ctl), stream);
+  if (rc != cudaSuccess) return rc;
+  rc = cudaMemcpyAsync(s.old_base, s.base, sizeof(int) * s.L.batch, cudaMemcpyDeviceToDevice, stream);
+  if (rc != cudaSuccess) return rc;
+  const int n_init = std::max(s.L.batch, s.nitems);
+  solve_init_kernel<T><<<(n_init + 255) / 256, 256, 0, stream>>>(a, s.warm);
+  if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+  if (s.warm != 1) {
+    prepare_kernel<T><<<dim3(8, s.L.batch), 256, 0, stream>>>(a, s.warm, s.old_base);
+    if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+  }
+  set_control_kernel<<<1, 1, 0, stream>>>(s.ctl, s.nitems, s.L.batch);
+  if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+  if (s.max_iters > 0) {
+    rc = cudaFuncSetAttribute(admm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)((size_t)lay.total * sizeof(T)));
+    if (rc != cudaSuccess) return rc;
+    void *params[] = {&a, &lay};
+    rc = cudaLaunchCooperativeKernel((const void *)admm_kernel<T>, dim3(s.grid), dim3(s.threads),
+                                     params, (size_t)lay.total * sizeof(T), stream);
+    if (rc != cudaSuccess) return rc;
+  }
+  output_kernel<T><<<dim3(4, s.L.batch), 256, 0, stream>>>(a, s.u_out, s.x_out);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 int admm_threads(int precision) { return precision == 0 ? 256 : 128; }
+int admm_iter_stride(int n, int precision) { return iter_stride(n, precision == 0 ? 4 : 8); }
+int admm_group_size(int n) { return group_size(n); }
 
-size_t admm_smem_bytes(int nx, int nu, int lti, int threads, int precision) {
-  Plan p = make_plan(nx, nu, lti, threads);
-  return precision == 0 ? plan_bytes<float>(p) : plan_bytes<double>(p);
+size_t admm_smem_bytes(const AdmmLaunch &s, int precision) {
+  if (precision == 0) return (size_t)layout_of<float>(s).total * 4;
+  return (size_t)layout_of<double>(s).total * 8;
 }
 
 cudaError_t admm_configure(int precision, size_t smem, int *blocks_per_sm) {
@@ -435,36 +723,8 @@ cudaError_t admm_configure(int precision, size_t smem, int *blocks_per_sm) {
   return rc;
 }
 
-template <typename T>
-static AdmmArgs<T> make_args(const AdmmLaunch &s) {
-  AdmmArgs<T> a;
-  a.L = s.L;
-  a.blk = (const T *)s.blk;
-  a.it[0] = (T *)s.it0;
-  a.it[1] = (T *)s.it1;
-  a.cur = s.cur;
-  a.qd = (const T *)s.qd;
-  a.ref = (const T *)s.ref;
-  a.ref_per_stage = s.ref_per_stage;
-  a.lo = (const T *)s.lo;
-  a.hi = (const T *)s.hi;
-  a.xb0 = (const T *)s.xb0;
-  a.rho = s.rho; a.eps = s.eps; a.eta = s.eta;
-  a.max_iters = s.max_iters; a.accel = s.accel;
-  a.mask = s.mask; a.mask_len = s.mask_len;
-  a.order = s.order; a.counter = s.counter; a.st = s.st;
-  a.u_out = s.u_out; a.x_out = s.x_out; a.warm = s.warm;
-  return a;
-}
-
-cudaError_t launch_admm(const AdmmLaunch &s, int precision, int grid, size_t smem,
-                        cudaStream_t stream) {
-  const int threads = admm_threads(precision);
-  if (precision == 0)
-    admm_kernel<float><<<grid, threads, smem, stream>>>(make_args<float>(s));
-  else
-    admm_kernel<double><<<grid, threads, smem, stream>>>(make_args<double>(s));
-  return cudaGetLastError();
+cudaError_t launch_admm(const AdmmLaunch &s, int precision, cudaStream_t stream) {
+  return precision == 0 ? launch_t<float>(s, stream) : launch_t<double>(s, stream);
 }
 
 }  // namespace pimpc

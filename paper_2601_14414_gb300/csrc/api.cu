@@ -11,6 +11,7 @@
 
 #include "launch.h"
 #include "pimpc.h"
+#include "solver.h"
 
 using namespace pimpc;
 
@@ -24,41 +25,7 @@ namespace {
 thread_local std::string g_create_error;
 }
 
-struct pimpc_solver {
-  int device = 0, batch = 0, lti = 0, prec = 0;
-  std::vector<int> nx, nu, N, W;
-  std::vector<int64_t> off_nx, off_nu, off_n, Nnx, Nnu, Nn, offA, offB, offe, blk, stage0, bbase;
-  int64_t tot_nx = 0, tot_nu = 0, tot_n = 0, tot_Nnx = 0, tot_Nnu = 0, tot_Nn = 0;
-  int64_t tot_A = 0, tot_B = 0, tot_e = 0, tot_blk = 0, nblocks = 0, stage_words = 0;
-  int max_nx = 0, max_n = 0;
-  Layout L{};
-  std::vector<void *> allocs;
-  // device buffers
-  double *A64 = nullptr, *B64 = nullptr, *e64 = nullptr;
-  double *qd64 = nullptr, *rdu64 = nullptr, *stage64 = nullptr;
-  double *out_u = nullptr, *out_x = nullptr;
-  void *blk_T = nullptr, *it0 = nullptr, *it1 = nullptr, *qd_T = nullptr, *ref_T = nullptr;
-  void *lo_T = nullptr, *hi_T = nullptr, *xb0_T = nullptr;
-  int *cur = nullptr, *order = nullptr, *counter = nullptr, *binst = nullptr, *ferr = nullptr;
-  int64_t *d_bbase = nullptr;
-  InstState *st = nullptr;
-  unsigned char *mask = nullptr, *mask_alloc = nullptr;
-  int mask_len = 0;
-  // options and state
-  double rho = 1.0, eps = 1e-6, eta = 0.999;
-  int max_iters = 1000, accel = 1;
-  bool stale = true, have_rdu = false, solved = false;
-  int last_ref_per_stage = 0, last_warm = 0, last_accel = 0, last_iters_fixed = 0;
-  double last_eps = 0.0;
-  size_t smem_admm = 0;
-  int grid_admm = 0;
-  std::string err;
-  // adjoint workspace (allocated by the first pimpc_backward)
-  void *adj_ws = nullptr;
-  size_t adj_ws_bytes = 0;
-};
-
-namespace {
+namespace pimpc {
 
 int fail(pimpc_solver *s, int code, const std::string &msg) {
   if (s) s->err = msg;
@@ -70,11 +37,21 @@ int cuda_fail(pimpc_solver *s, cudaError_t e, const char *what) {
   return fail(s, PIMPC_ECUDA, m);
 }
 
-#define PIMPC_CHECK(s, expr, what)                  \
-  do {                                              \
-    cudaError_t _e = (expr);                        \
-    if (_e != cudaSuccess) return cuda_fail((s), _e, (what)); \
-  } while (0)
+size_t tsize(int prec) { return prec == PIMPC_F32 ? 4 : 8; }
+
+cudaError_t dev_in(pimpc_solver *s, const double *p, int64_t count, int mem, int64_t at,
+                   cudaStream_t st, const double **out) {
+  if (!p) { *out = nullptr; return cudaSuccess; }
+  if (mem == PIMPC_DEVICE) { *out = p; return cudaSuccess; }
+  double *dst = s->stage64 + at;
+  cudaError_t e = cudaMemcpyAsync(dst, p, sizeof(double) * count, cudaMemcpyHostToDevice, st);
+  *out = dst;
+  return e;
+}
+
+}  // namespace pimpc
+
+namespace {
 
 template <typename P>
 cudaError_t dalloc(pimpc_solver *s, P **p, size_t bytes) {
@@ -84,20 +61,6 @@ cudaError_t dalloc(pimpc_solver *s, P **p, size_t bytes) {
   s->allocs.push_back(q);
   *p = (P *)q;
   return cudaSuccess;
-}
-
-size_t tsize(int prec) { return prec == PIMPC_F32 ? 4 : 8; }
-
-// Device view of a caller array: the pointer itself for device memory, else a copy in the
-// staging buffer at element offset `at`.
-cudaError_t dev_in(pimpc_solver *s, const double *p, int64_t count, int mem, int64_t at,
-                   cudaStream_t st, const double **out) {
-  if (!p) { *out = nullptr; return cudaSuccess; }
-  if (mem == PIMPC_DEVICE) { *out = p; return cudaSuccess; }
-  double *dst = s->stage64 + at;
-  cudaError_t e = cudaMemcpyAsync(dst, p, sizeof(double) * count, cudaMemcpyHostToDevice, st);
-  *out = dst;
-  return e;
 }
 
 bool finite_or_inf_ok(const double *p, int64_t n) {
@@ -152,14 +115,20 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   s->nx.assign(nx, nx + batch); s->nu.assign(nu, nu + batch); s->N.assign(N, N + batch);
   auto grow = [&](std::vector<int64_t> &v, int64_t &tot, int64_t add) { v.push_back(tot); tot += add; };
   const int threads = admm_threads(precision);
+  const size_t ts = tsize(precision);
+  int S_max = 1, nv_max = 2, W_max = 4, n5p_max = 4;
+  int64_t capB = 0, capI = 0;
+  int64_t stage_acc = 0;
   for (int j = 0; j < batch; ++j) {
     const int n = nx[j] + nu[j];
+    const int n5p = admm_iter_stride(n, precision);
     grow(s->off_nx, s->tot_nx, nx[j]);
     grow(s->off_nu, s->tot_nu, nu[j]);
     grow(s->off_n, s->tot_n, n);
     grow(s->Nnx, s->tot_Nnx, (int64_t)N[j] * nx[j]);
     grow(s->Nnu, s->tot_Nnu, (int64_t)N[j] * nu[j]);
     grow(s->Nn, s->tot_Nn, (int64_t)N[j] * n);
+    grow(s->Ni, s->tot_Ni, (int64_t)N[j] * n5p);
     const int64_t reps = lti ? 1 : N[j];
     grow(s->offA, s->tot_A, reps * nx[j] * nx[j]);
     grow(s->offB, s->tot_B, reps * nx[j] * nu[j]);
@@ -167,46 +136,95 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
     const int w = block_words(nx[j], nu[j]);
     s->W.push_back(w);
     grow(s->blk, s->tot_blk, (int64_t)blocks_per_instance(lti, N[j]) * w);
-    s->stage0.push_back(s->bbase.empty() ? 0 : s->stage0.back() + N[j - 1]);
+    s->stage0.push_back(stage_acc);
+    stage_acc += N[j];
     grow(s->bbase, s->nblocks, blocks_per_instance(lti, N[j]));
     s->max_nx = std::max(s->max_nx, nx[j]);
     s->max_n = std::max(s->max_n, n);
-    s->smem_admm = std::max(s->smem_admm, admm_smem_bytes(nx[j], nu[j], lti, threads, precision));
+    const int S = threads / admm_group_size(n);
+    S_max = std::max(S_max, S);
+    nv_max = std::max(nv_max, (n + 1) & ~1);
+    W_max = std::max(W_max, w);
+    n5p_max = std::max(n5p_max, n5p);
+    if (!lti) capB = std::max<int64_t>(capB, (int64_t)(S + 1) * w);
+    capI = std::max<int64_t>(capI, (int64_t)(S + 1) * n5p);
   }
+  // Shared-memory plan of the persistent solve kernel.
+  AdmmLaunch &P = s->plan;
+  P.capB = (int)capB;
+  P.capI = (int)capI;
+  P.haloB = lti ? 2 * W_max : W_max;
+  P.haloI = 2 * n5p_max;
+  P.S_max = S_max;
+  P.nv_max = nv_max;
+  P.threads = threads;
+  s->smem_admm = admm_smem_bytes(P, precision);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  if (s->smem_admm > (size_t)optin - 1024) {
+  if (s->smem_admm + 1024 > (size_t)optin) {
     g_create_error = "an instance needs more shared memory than one CTA has at this precision";
     delete s;
     return PIMPC_EINVAL;
   }
-  const size_t ts = tsize(precision);
-  std::vector<int> binst(s->nblocks);
-  for (int j = 0; j < batch; ++j)
-    for (int b = 0; b < blocks_per_instance(lti, N[j]); ++b) binst[s->bbase[j] + b] = j;
-  // Work order: largest streamed volume first.
+  // Instance order (largest streamed volume first) and its work items.
   std::vector<int> order(batch);
   std::iota(order.begin(), order.end(), 0);
   std::vector<double> cost(batch);
+  int64_t total_sub = 0;
   for (int j = 0; j < batch; ++j) {
     const int n = nx[j] + nu[j];
     cost[j] = (double)N[j] * ((lti ? 0 : s->W[j]) + 15.0 * n);
+    const int S = threads / admm_group_size(n);
+    total_sub += (N[j] + S - 1) / S;
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  int bps = 0, nsm = 0;
+  cudaError_t e = admm_configure(precision, s->smem_admm, &bps);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess || bps < 1) {
+    g_create_error = std::string("kernel configuration failed: ") +
+                     (e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy");
+    delete s;
+    return PIMPC_ECUDA;
+  }
+  const int64_t max_grid = (int64_t)bps * nsm;
+  // Sub-chunks per item: enough items for about 4 per CTA, at most 16 sub-chunks per item.
+  int64_t m = total_sub / (4 * max_grid);
+  m = std::max<int64_t>(1, std::min<int64_t>(16, m));
+  std::vector<int> item_inst, item_a, item_b, nitems_inst(batch, 0);
+  for (int oi = 0; oi < batch; ++oi) {
+    const int j = order[oi];
+    const int n = nx[j] + nu[j];
+    const int S = threads / admm_group_size(n);
+    int is = (int)(S * m);
+    if (lti) is = std::max(is, std::min(N[j], (256 + S - 1) / S * S));
+    for (int a0 = 0; a0 < N[j]; a0 += is) {
+      item_inst.push_back(j);
+      item_a.push_back(a0);
+      item_b.push_back(std::min(N[j], a0 + is));
+      nitems_inst[j] += 1;
+    }
+  }
+  s->nitems = (int)item_inst.size();
+  s->grid_admm = (int)std::min<int64_t>(max_grid, s->nitems);
+  P.grid = s->grid_admm;
+
+  std::vector<int> binst(s->nblocks);
+  for (int j = 0; j < batch; ++j)
+    for (int b = 0; b < blocks_per_instance(lti, N[j]); ++b) binst[s->bbase[j] + b] = j;
 
   const int64_t stage_words = std::max<int64_t>(
       {2 * s->tot_nx + 2 * s->tot_nu, s->tot_nx + s->tot_nu + s->tot_Nn,
        s->tot_Nnx + s->tot_Nnu + 8 * (int64_t)batch, s->tot_Nnx + s->tot_Nnu + 2 * s->tot_Nn,
        s->tot_n + s->tot_Nn});
   s->stage_words = stage_words;
-  cudaError_t e = cudaSuccess;
+  e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  std::vector<int64_t *> d64;
-  int64_t *d_off[13];
   std::vector<int64_t> *h_off[13] = {&s->off_nx, &s->off_nu, &s->off_n, &s->Nnx, &s->Nnu, &s->Nn,
                                      &s->offA, &s->offB, &s->offe, &s->blk, &s->stage0, &s->bbase,
-                                     nullptr};
-  for (int i = 0; i < 12; ++i) {
+                                     &s->Ni};
+  int64_t *d_off[13];
+  for (int i = 0; i < 13; ++i) {
     chk(dalloc(s, &d_off[i], sizeof(int64_t) * batch));
     if (e == cudaSuccess) chk(cudaMemcpy(d_off[i], h_off[i]->data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   }
@@ -230,26 +248,41 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(dalloc(s, &s->out_u, sizeof(double) * s->tot_Nnu));
   chk(dalloc(s, &s->out_x, sizeof(double) * s->tot_Nnx));
   chk(dalloc(s, &s->blk_T, ts * s->tot_blk));
-  chk(dalloc(s, &s->it0, ts * 5 * s->tot_Nn));
-  chk(dalloc(s, &s->it1, ts * 5 * s->tot_Nn));
+  for (int b = 0; b < 3; ++b) chk(dalloc(s, &s->it[b], ts * s->tot_Ni));
   chk(dalloc(s, &s->qd_T, ts * s->tot_n));
   chk(dalloc(s, &s->ref_T, ts * std::max(s->tot_Nn, s->tot_n)));
   chk(dalloc(s, &s->lo_T, ts * s->tot_n));
   chk(dalloc(s, &s->hi_T, ts * s->tot_n));
   chk(dalloc(s, &s->xb0_T, ts * s->tot_n));
-  chk(dalloc(s, &s->cur, sizeof(int) * batch));
-  chk(dalloc(s, &s->order, sizeof(int) * batch));
-  chk(dalloc(s, &s->counter, sizeof(int) * 4));
+  chk(dalloc(s, &s->base, sizeof(int) * batch));
+  chk(dalloc(s, &s->old_base, sizeof(int) * batch));
+  chk(dalloc(s, &s->alpha, sizeof(double) * batch));
+  chk(dalloc(s, &s->cprev, sizeof(double) * batch));
+  chk(dalloc(s, &s->coef, sizeof(double) * batch));
+  chk(dalloc(s, &s->cacc, sizeof(double) * batch));
+  chk(dalloc(s, &s->ndone, sizeof(int) * batch));
+  chk(dalloc(s, &s->stop, sizeof(int) * batch));
+  chk(dalloc(s, &s->item_inst, sizeof(int) * s->nitems));
+  chk(dalloc(s, &s->item_a, sizeof(int) * s->nitems));
+  chk(dalloc(s, &s->item_b, sizeof(int) * s->nitems));
+  chk(dalloc(s, &s->nitems_inst, sizeof(int) * batch));
+  chk(dalloc(s, &s->list0, sizeof(int) * s->nitems));
+  chk(dalloc(s, &s->list1, sizeof(int) * s->nitems));
+  chk(dalloc(s, &s->ctl, sizeof(Ctl)));
   chk(dalloc(s, &s->binst, sizeof(int) * s->nblocks));
   chk(dalloc(s, &s->ferr, sizeof(int) * 4));
   chk(dalloc(s, &s->st, sizeof(InstState) * batch));
   if (e != cudaSuccess) {
     g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
+    const bool oom = e == cudaErrorMemoryAllocation;
     pimpc_destroy(s);
-    return e == cudaErrorMemoryAllocation ? PIMPC_ENOMEM : PIMPC_ECUDA;
+    return oom ? PIMPC_ENOMEM : PIMPC_ECUDA;
   }
   s->d_bbase = d_off[11];
-  chk(cudaMemcpy(s->order, order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_inst, item_inst.data(), sizeof(int) * s->nitems, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_a, item_a.data(), sizeof(int) * s->nitems, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_b, item_b.data(), sizeof(int) * s->nitems, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->nitems_inst, nitems_inst.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(s->binst, binst.data(), sizeof(int) * s->nblocks, cudaMemcpyHostToDevice));
   chk(cudaMemset(s->A64, 0, sizeof(double) * s->tot_A));
   chk(cudaMemset(s->B64, 0, sizeof(double) * s->tot_B));
@@ -257,12 +290,10 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(cudaMemset(s->qd64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->rdu64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->qd_T, 0, ts * s->tot_n));
-  chk(cudaMemset(s->it0, 0, ts * 5 * s->tot_Nn));
-  chk(cudaMemset(s->it1, 0, ts * 5 * s->tot_Nn));
-  chk(cudaMemset(s->cur, 0, sizeof(int) * batch));
+  for (int b = 0; b < 3; ++b) chk(cudaMemset(s->it[b], 0, ts * s->tot_Ni));
+  chk(cudaMemset(s->base, 0, sizeof(int) * batch));
   chk(cudaMemset(s->ferr, 0, sizeof(int) * 4));
   chk(cudaMemset(s->st, 0, sizeof(InstState) * batch));
-  // Infinite bounds by default.
   {
     std::vector<double> inf(s->tot_n, INFINITY);
     chk(cudaMemcpy(s->stage64, inf.data(), sizeof(double) * s->tot_n, cudaMemcpyHostToDevice));
@@ -272,22 +303,17 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
     chk(launch_convert(s->stage64, s->tot_n, precision, s->lo_T, 0));
     chk(cudaDeviceSynchronize());
   }
+  if (e != cudaSuccess) {
+    g_create_error = std::string("device initialisation failed: ") + cudaGetErrorString(e);
+    pimpc_destroy(s);
+    return PIMPC_ECUDA;
+  }
   Layout &L = s->L;
   L.batch = batch; L.lti = lti; L.nx = d_nx; L.nu = d_nu; L.N = d_N;
   L.off_nx = d_off[0]; L.off_nu = d_off[1]; L.off_n = d_off[2];
   L.Nnx = d_off[3]; L.Nnu = d_off[4]; L.Nn = d_off[5];
   L.offA = d_off[6]; L.offB = d_off[7]; L.offe = d_off[8];
-  L.blk = d_off[9]; L.W = d_W; L.stage0 = d_off[10];
-  int bps = 0, nsm = 0;
-  chk(admm_configure(precision, s->smem_admm, &bps));
-  chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-  if (e != cudaSuccess || bps < 1) {
-    g_create_error = std::string("kernel configuration failed: ") +
-                     (e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy");
-    pimpc_destroy(s);
-    return PIMPC_ECUDA;
-  }
-  s->grid_admm = std::min(batch, bps * nsm);
+  L.blk = d_off[9]; L.W = d_W; L.stage0 = d_off[10]; L.Ni = d_off[12];
   *out = s;
   return PIMPC_OK;
 }
@@ -441,18 +467,24 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
   PIMPC_CHECK(s, dev_in(s, ref, nref, mem, s->tot_nx + s->tot_nu, st, &dref), "copy ref");
   PIMPC_CHECK(s, launch_gather_n(s->L, dx0, dup, s->tot_n, s->prec, s->xb0_T, st), "x0");
   if (dref) PIMPC_CHECK(s, launch_convert(dref, nref, s->prec, s->ref_T, st), "ref");
-  PIMPC_CHECK(s, cudaMemsetAsync(s->counter, 0, sizeof(int), st), "reset queue");
-  AdmmLaunch a;
-  a.L = s->L; a.blk = s->blk_T; a.it0 = s->it0; a.it1 = s->it1; a.cur = s->cur;
+  AdmmLaunch a = s->plan;
+  a.L = s->L; a.blk = s->blk_T;
+  for (int b = 0; b < 3; ++b) a.it[b] = s->it[b];
   a.qd = s->qd_T; a.ref = dref ? s->ref_T : nullptr; a.ref_per_stage = ref_per_stage;
   a.lo = s->lo_T; a.hi = s->hi_T; a.xb0 = s->xb0_T;
   a.rho = s->rho; a.eps = s->eps; a.eta = s->eta; a.max_iters = s->max_iters; a.accel = s->accel;
-  a.mask = s->mask; a.mask_len = s->mask_len; a.order = s->order; a.counter = s->counter;
-  a.st = s->st; a.warm = warm_start;
+  a.mask = s->mask; a.mask_len = s->mask_len;
+  a.item_inst = s->item_inst; a.item_a = s->item_a; a.item_b = s->item_b;
+  a.nitems_inst = s->nitems_inst; a.nitems = s->nitems;
+  a.list0 = s->list0; a.list1 = s->list1; a.ctl = s->ctl;
+  a.base = s->base; a.old_base = s->old_base; a.st = s->st;
+  a.alpha = s->alpha; a.cprev = s->cprev; a.coef = s->coef; a.cacc = s->cacc;
+  a.ndone = s->ndone; a.stop = s->stop;
+  a.warm = warm_start;
   const bool dev = mem == PIMPC_DEVICE;
   a.u_out = u_out ? (dev ? u_out : s->out_u) : nullptr;
   a.x_out = x_out ? (dev ? x_out : s->out_x) : nullptr;
-  PIMPC_CHECK(s, launch_admm(a, s->prec, s->grid_admm, s->smem_admm, st), "solve");
+  PIMPC_CHECK(s, launch_admm(a, s->prec, st), "solve");
   s->solved = true;
   s->last_ref_per_stage = ref_per_stage;
   s->last_warm = warm_start;
@@ -489,17 +521,16 @@ int pimpc_get_iterates(pimpc_solver *s, double *z, double *v, double *theta, dou
   cudaSetDevice(s->device);
   double *outs[5] = {z, v, theta, beta, lambda};
   if (mem == PIMPC_DEVICE) {
-    PIMPC_CHECK(s, launch_export_iterates(s->L, s->it0, s->it1, s->cur, s->tot_Nn, s->prec, z, v,
-                                          theta, beta, lambda, st), "export");
+    PIMPC_CHECK(s, launch_export_iterates(s->L, s->it, s->base, s->prec, z, v, theta, beta, lambda, st),
+                "export");
     return PIMPC_OK;
   }
-  // Host: export one array at a time through the staging buffer.
   for (int b = 0; b < 5; ++b) {
     if (!outs[b]) continue;
     double *tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     tmp[b] = s->stage64;
-    PIMPC_CHECK(s, launch_export_iterates(s->L, s->it0, s->it1, s->cur, s->tot_Nn, s->prec, tmp[0],
-                                          tmp[1], tmp[2], tmp[3], tmp[4], st), "export");
+    PIMPC_CHECK(s, launch_export_iterates(s->L, s->it, s->base, s->prec, tmp[0], tmp[1], tmp[2],
+                                          tmp[3], tmp[4], st), "export");
     PIMPC_CHECK(s, cudaMemcpyAsync(outs[b], s->stage64, sizeof(double) * s->tot_Nn, cudaMemcpyDeviceToHost, st), "copy iterates");
     PIMPC_CHECK(s, cudaStreamSynchronize(st), "get_iterates");
   }

@@ -4,7 +4,8 @@
 //   K = Qbar + rho I + rho Abar_{k+1}^T Abar_{k+1}   (k < N-1),   K = Qbar + rho I   (k = N-1),
 // where Abar^T Abar = G^T G + diag(0, I_nu) with G = [A | B] (Theorem 2's velocity form), factors
 // K = L L^T (Cholesky) and writes H_k = K^{-1}, obtained column by column from L y = e_c and
-// L^T x = y. It also writes M_k = (B_k^T B_k + I + Wdu / rho)^{-1}, so that the du update of
+// L^T x = y, stored diagonal by diagonal (the layout the iteration reads with consecutive lanes
+// on consecutive words). It also writes M_k = (B_k^T B_k + I + Wdu / rho)^{-1}, so that the du update of
 // Algorithm 1 step 1, J_k (v - beta) with J_k = (Bbar^T Bbar)^{-1} Bbar^T, is
 // M_k (B_k^T (v - beta)_x + (v - beta)_u); and it copies G_k and e_k into the stage block.
 // Outputs are converted to the iteration precision T. LTI instances have two blocks: block 0
@@ -119,8 +120,9 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   const int W = a.L.W[j];
   T *out = blk + a.L.blk[j] + (int64_t)kb * W;
   const int oE = nx * n, oH = oE + nx, oM = oH + n * (n + 1) / 2;
-  for (int i = 0; i < n; ++i)
-    for (int c = lane; c <= i; c += 32) out[oH + i * (i + 1) / 2 + c] = (T)X[i * ld + c];
+  // H_k diagonal by diagonal: diagonal d at d n - d (d - 1) / 2 holds H[i][i + d].
+  for (int d = 0; d < n; ++d)
+    for (int i = lane; i < n - d; i += 32) out[oH + d * n - d * (d - 1) / 2 + i] = (T)X[i * ld + i + d];
   __syncwarp();
 
   // Own-stage G_k, e_k and M_k = (B_k^T B_k + I + Wdu/rho)^{-1}.
@@ -142,8 +144,8 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
       S[i * nu + c] = s;
     }
   chol_inverse(S, X, nu, nu, lane, a.err);
-  for (int i = 0; i < nu; ++i)
-    for (int c = lane; c <= i; c += 32) out[oM + i * (i + 1) / 2 + c] = (T)X[i * nu + c];
+  for (int d = 0; d < nu; ++d)
+    for (int i = lane; i < nu - d; i += 32) out[oM + d * nu - d * (d - 1) / 2 + i] = (T)X[i * nu + i + d];
   for (int w = oM + nu * (nu + 1) / 2 + lane; w < W; w += 32) out[w] = (T)0;
 }
 

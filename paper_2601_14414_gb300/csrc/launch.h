@@ -13,8 +13,7 @@ cudaError_t launch_factorise(const Layout &L, const double *A, const double *B, 
 struct AdmmLaunch {
   Layout L;
   const void *blk;
-  void *it0, *it1;
-  int *cur;
+  void *it[3];
   const void *qd, *ref;
   int ref_per_stage;
   const void *lo, *hi, *xb0;
@@ -22,19 +21,30 @@ struct AdmmLaunch {
   int max_iters, accel;
   const unsigned char *mask;
   int mask_len;
-  const int *order;
-  int *counter;
+  // work items
+  const int *item_inst, *item_a, *item_b, *nitems_inst;
+  int nitems;
+  int *list0, *list1;
+  Ctl *ctl;
+  // per-instance state
+  int *base, *old_base;
   InstState *st;
+  double *alpha, *cprev, *coef, *cacc;
+  int *ndone, *stop;
   double *u_out, *x_out;
   int warm;
+  // launch shape and shared-memory plan (elements of the iteration type)
+  int grid, threads;
+  int capB, capI, haloB, haloI, S_max, nv_max;
 };
 
-// Shared-memory bytes the ADMM kernel needs for an instance with these sizes.
-size_t admm_smem_bytes(int nx, int nu, int lti, int threads, int precision);
+__global__ void set_control_kernel(Ctl *c, int nitems, int batch);
 int admm_threads(int precision);
+int admm_iter_stride(int n, int precision);
+int admm_group_size(int n);
+size_t admm_smem_bytes(const AdmmLaunch &s, int precision);
 cudaError_t admm_configure(int precision, size_t smem, int *blocks_per_sm);
-cudaError_t launch_admm(const AdmmLaunch &a, int precision, int grid, size_t smem,
-                        cudaStream_t stream);
+cudaError_t launch_admm(const AdmmLaunch &a, int precision, cudaStream_t stream);
 
 // Elementwise helpers.
 cudaError_t launch_gather_n(const Layout &L, const double *xpart, const double *upart,
@@ -43,10 +53,9 @@ cudaError_t launch_gather_n64(const Layout &L, const double *xpart, const double
                               int64_t total_n, double *dst, cudaStream_t stream);
 cudaError_t launch_convert(const double *src, int64_t count, int precision, void *dst,
                            cudaStream_t stream);
-cudaError_t launch_export_iterates(const Layout &L, const void *it0, const void *it1,
-                                   const int *cur, int64_t total_stage_n, int precision,
-                                   double *z, double *v, double *th, double *be, double *la,
-                                   cudaStream_t stream);
+cudaError_t launch_export_iterates(const Layout &L, void *const *it, const int *base,
+                                   int precision, double *z, double *v, double *th, double *be,
+                                   double *la, cudaStream_t stream);
 
 // Models.
 int model_nparams(int model);

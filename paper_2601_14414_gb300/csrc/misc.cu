@@ -26,18 +26,21 @@ __global__ void convert_kernel(const double *src, int64_t count, T *dst) {
     dst[i] = (T)src[i];
 }
 
-// Iterates of stage k: [z | v | theta | beta | lambda] (5 n) -> five [sum N n] FP64 arrays.
+// Iterates of stage k: [z | v | theta | beta | lambda] (stride n5p) -> five [sum N n] FP64 arrays.
 template <typename T>
-__global__ void export_kernel(Layout L, const T *it0, const T *it1, const int *cur, double *z,
+__global__ void export_kernel(Layout L, T *it0, T *it1, T *it2, const int *base, double *z,
                               double *v, double *th, double *be, double *la) {
   const int j = blockIdx.x;
   const int n = L.nx[j] + L.nu[j], N = L.N[j];
-  const T *src = (cur[j] ? it1 : it0) + 5 * L.Nn[j];
+  const int q = 16 / (int)sizeof(T);
+  const int n5p = (5 * n + q - 1) / q * q;
+  T *bufs[3] = {it0, it1, it2};
+  const T *src = bufs[base[j]] + L.Ni[j];
   double *outs[5] = {z, v, th, be, la};
   for (int64_t t = threadIdx.x; t < (int64_t)N * n; t += blockDim.x) {
     const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
     for (int b = 0; b < 5; ++b)
-      if (outs[b]) outs[b][L.Nn[j] + t] = (double)src[(int64_t)k * 5 * n + b * n + c];
+      if (outs[b]) outs[b][L.Nn[j] + t] = (double)src[(int64_t)k * n5p + b * n + c];
   }
 }
 
@@ -72,17 +75,15 @@ cudaError_t launch_convert(const double *src, int64_t count, int precision, void
   return cudaGetLastError();
 }
 
-cudaError_t launch_export_iterates(const Layout &L, const void *it0, const void *it1,
-                                   const int *cur, int64_t total_stage_n, int precision,
-                                   double *z, double *v, double *th, double *be, double *la,
-                                   cudaStream_t stream) {
-  (void)total_stage_n;
+cudaError_t launch_export_iterates(const Layout &L, void *const *it, const int *base,
+                                   int precision, double *z, double *v, double *th, double *be,
+                                   double *la, cudaStream_t stream) {
   if (precision == 0)
-    export_kernel<float><<<L.batch, 256, 0, stream>>>(L, (const float *)it0, (const float *)it1,
-                                                      cur, z, v, th, be, la);
+    export_kernel<float><<<L.batch, 256, 0, stream>>>(L, (float *)it[0], (float *)it[1],
+                                                      (float *)it[2], base, z, v, th, be, la);
   else
-    export_kernel<double><<<L.batch, 256, 0, stream>>>(L, (const double *)it0,
-                                                       (const double *)it1, cur, z, v, th, be, la);
+    export_kernel<double><<<L.batch, 256, 0, stream>>>(L, (double *)it[0], (double *)it[1],
+                                                       (double *)it[2], base, z, v, th, be, la);
   return cudaGetLastError();
 }
 

@@ -6,14 +6,15 @@
 //   offA[j] (sum N nx^2, or sum nx^2 when lti), offB[j], offe[j].
 //
 // Stage block (iteration precision T), the unit the ADMM kernel streams. For one stage k:
-//   [ G_k = [A_k | B_k] : nx x n row-major ][ e_k : nx ][ H_k : packed lower, n(n+1)/2 ]
-//   [ M_k : packed lower, nu(nu+1)/2 ], padded to a multiple of 4 elements (W words).
-// Packed lower row-major: element (i, j), j <= i, at i(i+1)/2 + j. An LTV instance has N blocks at
-// blk[j] + k W; an LTI instance has two: block 0 (H = H_k, k < N-1) and block 1 (H = H_{N-1}).
+//   [ G_k = [A_k | B_k] : nx x n row-major ][ e_k : nx ][ H_k : n(n+1)/2 ][ M_k : nu(nu+1)/2 ],
+// padded to a multiple of 4 elements (W words). The symmetric H_k and M_k are stored diagonal by
+// diagonal: diagonal d of an m x m matrix starts at d m - d (d - 1) / 2 and holds A[i][i + d],
+// i = 0 .. m-1-d. An LTV instance has N blocks at blk[j] + k W; an LTI instance has two: block 0
+// (H = H_k, k < N-1) and block 1 (H = H_{N-1}).
 //
-// Iterates (T): two buffers it[0], it[1]; stage k of instance j holds [z | v | theta | beta |
-// lambda] (5 n values, z = z_{k+1}) at 5 Nn[j] + 5 n k. cur[j] says which buffer holds the latest
-// non-hat iterate; the other holds the one before it (used by the momentum step).
+// Iterates (T): three rotating buffers it[0..2]; stage k of instance j holds [z | v | theta | beta |
+// lambda] (5 n values, z = z_{k+1}, padded to a 16-byte multiple n5p) at Ni[j] + n5p k. base[j]
+// names the buffer with the latest non-hat iterate after a solve.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,6 +24,7 @@ namespace pimpc {
 constexpr int kConverged = 0;   // per-instance status codes (same values as the C ABI)
 constexpr int kMaxIter = 1;
 constexpr int kNonFinite = 2;
+constexpr int kTimeout = 3;
 constexpr int kMaxNLtv = 32;
 constexpr int kMaxNLti = 64;
 
@@ -36,6 +38,19 @@ struct Layout {
   const int64_t *blk;              // stage-block offsets (elements of T)
   const int *W;                    // stage-block size (elements)
   const int64_t *stage0;           // global index of the instance's first stage
+  const int64_t *Ni;               // iterate offsets: sum_{i<j} N_i n5p_i
+};
+
+// Control block of one persistent solve launch.
+struct Ctl {
+  int queue[2];          // item queue counters (alternating iterations)
+  unsigned bar_count;    // grid barrier: arrivals and generation
+  unsigned bar_gen;
+  int active;            // instances still iterating
+  int stopped;           // some instance stopped in this iteration
+  int err;               // nonzero: a bounded wait timed out
+  int nlist[2];          // lengths of the two active-item lists
+  int pad[7];
 };
 
 __host__ __device__ inline int packed_size(int n) { return n * (n + 1) / 2; }

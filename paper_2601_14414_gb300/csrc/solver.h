@@ -1,0 +1,62 @@
+// solver.h -- the solver object behind the opaque pimpc_solver handle (internal to the library).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+struct pimpc_solver {
+  int device = 0, batch = 0, lti = 0, prec = 0;
+  std::vector<int> nx, nu, N, W;
+  std::vector<int64_t> off_nx, off_nu, off_n, Nnx, Nnu, Nn, Ni, offA, offB, offe, blk, stage0, bbase;
+  int64_t tot_nx = 0, tot_nu = 0, tot_n = 0, tot_Nnx = 0, tot_Nnu = 0, tot_Nn = 0, tot_Ni = 0;
+  int64_t tot_A = 0, tot_B = 0, tot_e = 0, tot_blk = 0, nblocks = 0, stage_words = 0;
+  int max_nx = 0, max_n = 0;
+  pimpc::Layout L{};
+  std::vector<void *> allocs;
+  // device buffers
+  double *A64 = nullptr, *B64 = nullptr, *e64 = nullptr;
+  double *qd64 = nullptr, *rdu64 = nullptr, *stage64 = nullptr;
+  double *out_u = nullptr, *out_x = nullptr;
+  void *blk_T = nullptr, *qd_T = nullptr, *ref_T = nullptr;
+  void *it[3] = {nullptr, nullptr, nullptr};
+  void *lo_T = nullptr, *hi_T = nullptr, *xb0_T = nullptr;
+  int *base = nullptr, *old_base = nullptr, *binst = nullptr, *ferr = nullptr;
+  double *alpha = nullptr, *cprev = nullptr, *coef = nullptr, *cacc = nullptr;
+  int *ndone = nullptr, *stop = nullptr;
+  int *item_inst = nullptr, *item_a = nullptr, *item_b = nullptr, *nitems_inst = nullptr;
+  int *list0 = nullptr, *list1 = nullptr;
+  pimpc::Ctl *ctl = nullptr;
+  int64_t *d_bbase = nullptr;
+  pimpc::InstState *st = nullptr;
+  unsigned char *mask = nullptr, *mask_alloc = nullptr;
+  int mask_len = 0;
+  int nitems = 0;
+  // options and state
+  double rho = 1.0, eps = 1e-6, eta = 0.999;
+  int max_iters = 1000, accel = 1;
+  bool stale = true, have_rdu = false, solved = false;
+  int last_ref_per_stage = 0, last_warm = 0, last_accel = 0, last_iters_fixed = 0;
+  double last_eps = 0.0;
+  size_t smem_admm = 0;
+  int grid_admm = 0;
+  pimpc::AdmmLaunch plan{};
+  std::string err;
+  // adjoint workspace (allocated by the first pimpc_backward)
+  void *adj_ws = nullptr;
+  size_t adj_ws_bytes = 0;
+};
+
+namespace pimpc {
+int fail(pimpc_solver *s, int code, const std::string &msg);
+int cuda_fail(pimpc_solver *s, cudaError_t e, const char *what);
+size_t tsize(int prec);
+cudaError_t dev_in(pimpc_solver *s, const double *p, int64_t count, int mem, int64_t at,
+                   cudaStream_t st, const double **out);
+}  // namespace pimpc
+
+#define PIMPC_CHECK(s, expr, what)                                       \
+  do {                                                                   \
+    cudaError_t _e = (expr);                                             \
+    if (_e != cudaSuccess) return pimpc::cuda_fail((s), _e, (what));     \
+  } while (0)

@@ -24,6 +24,13 @@ def relerr(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-12))
 
 
+def solution_error(u, x, u_ref, x_ref):
+    """max |w - w*| / max(1, max |w*|) over w = (u, x): the accuracy measure of the benchmark."""
+    w = np.concatenate([np.ravel(u), np.ravel(x)])
+    ws = np.concatenate([np.ravel(u_ref), np.ravel(x_ref)])
+    return float(np.max(np.abs(w - ws)) / max(1.0, np.max(np.abs(ws))))
+
+
 # (nx, nu, N): lane groups of 8, 16 and 32, ragged last chunks, N = 1, and several chunks.
 RAGGED = [(4, 2, 37), (14, 2, 19), (24, 8, 11), (3, 1, 70), (6, 2, 1), (12, 4, 33), (5, 3, 9),
           (20, 7, 45), (9, 9, 17)]
@@ -54,7 +61,8 @@ def test_fp64_fixed_iterations_match_oracle(accel):
         assert relerr(res["u"][j], o["u"]) <= 1e-10
         assert relerr(res["x"][j], o["x"]) <= 1e-10
         assert res["iters"][j] == 200 and res["status"][j] == pimpc.MAXITER
-        assert abs(res["c"][j] - o["c"]) <= 1e-8 * max(o["c"], 1e-30)
+        # c is a sum of squared changes; once an instance has converged it is rounding noise
+        assert abs(res["c"][j] - o["c"]) <= 1e-8 * o["c"] + 1e-24
 
 
 def test_fp32_plain_fixed_iterations_match_oracle():
@@ -87,8 +95,7 @@ def test_converged_fp32_matches_converged_oracle():
     ora = oracle_runs(insts, eps=1e-22, max_iters=200000, accel=1)
     for j, o in enumerate(ora):
         assert o["status"] == oracle.CONVERGED
-        assert relerr(res["u"][j], o["u"]) <= 1e-5
-        assert relerr(res["x"][j], o["x"]) <= 1e-5
+        assert solution_error(res["u"][j], res["x"][j], o["u"], o["x"]) <= 1e-5
 
 
 def test_lti_up_to_n64_fp64():
