@@ -1,4 +1,5 @@
-// admm.cu -- the piMPC iteration (Algorithm 1) on a batch of instances in one persistent launch.
+// admm.cu -- Algorithm 1 with a group of lanes per stage, used for stage-invariant instances
+// with 32 < n <= 64 (smaller instances use the one-thread-per-stage kernel of admm_tps.cu).
 //
 // Work decomposition. The stages of every instance are cut into items of consecutive stages
 // (item = instance j, stages [a, b)). One cooperative launch runs all iterations of all
@@ -35,7 +36,7 @@
 
 #include <algorithm>
 
-#include "launch.h"
+#include "lockstep.cuh"
 
 namespace pimpc {
 
@@ -47,7 +48,7 @@ __global__ void set_control_kernel(Ctl *c, int nitems, int batch) {
 
 namespace {
 
-constexpr long long kWaitLimit = 1ll << 22;  // bounded polls of an mbarrier / the grid barrier
+using ls::kWaitLimit;
 
 // ---------------------------------------------------------------------------------------------
 // PTX helpers: mbarrier + bulk asynchronous copies (the non-tensor TMA form).
@@ -86,32 +87,8 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// ---------------------------------------------------------------------------------------------
-// Kernel arguments.
-// ---------------------------------------------------------------------------------------------
 template <typename T>
-struct Args {
-  Layout L;
-  const T *blk;
-  T *it[3];
-  const T *qd, *ref;
-  int ref_per_stage;
-  const T *lo, *hi, *xb0;
-  double rho, eps, eta;
-  int max_iters, accel;
-  const unsigned char *mask;
-  int mask_len;
-  const int *item_inst, *item_a, *item_b;
-  int nitems;
-  const int *nitems_inst;
-  int *list[2];
-  Ctl *ctl;
-  int *base;
-  InstState *st;
-  double *alpha, *cprev, *coef, *cacc;
-  int *ndone, *stop;
-  int capI;  // elements of one iterate area (cur); prev follows at +capI
-};
+using Args = ls::Args<T>;
 
 __host__ __device__ inline int group_size(int n) { return n <= 8 ? 8 : (n <= 16 ? 16 : 32); }
 __host__ __device__ inline int iter_stride(int n, int tsize) {
@@ -144,34 +121,6 @@ __host__ __device__ inline Smem smem_layout(int capB, int capI, int haloB, int h
 template <typename T>
 __device__ inline T clampv(T x, T lo, T hi) {
   return x < lo ? lo : (x > hi ? hi : x);
-}
-
-// Bounded grid barrier; all CTAs of the cooperative launch are co-resident.
-__device__ bool grid_sync(Ctl *c, unsigned nblocks, int *sOk) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *gen = &c->bar_gen;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-    int ok = 1;
-    if (arrived == nblocks - 1) {
-      c->bar_count = 0;
-      __threadfence();
-      atomicAdd(&c->bar_gen, 1u);
-    } else {
-      long long k = 0;
-      while (*gen == g) {
-        if (++k > kWaitLimit || *(volatile int *)&c->err) { ok = 0; break; }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    if (!ok) atomicExch(&c->err, 1);
-    *sOk = ok && (*(volatile int *)&c->err == 0);
-  }
-  __syncthreads();
-  return *sOk != 0;
 }
 
 // Bounded wait on an mbarrier phase (every thread polls); false and an error flag on timeout.
@@ -490,79 +439,13 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
       if (tid == 0) {
         double part = 0.0;
         for (int w = 0; w < (nthreads >> 5); ++w) part += sRed[w];
-        atomicAdd(&a.cacc[j], part);
-        __threadfence();
-        const int done = atomicAdd(&a.ndone[j], 1);
-        if (done == a.nitems_inst[j] - 1) {
-          __threadfence();
-          const double s = __longlong_as_double(
-              (long long)atomicExch((unsigned long long *)&a.cacc[j], 0ull));
-          a.ndone[j] = 0;
-          const double c = a.rho * s;
-          InstState &st = a.st[j];
-          st.iters = it + 1;
-          st.c = c;
-          int stop = 0;
-          if (!isfinite(c)) {
-            st.status = kNonFinite; stop = 1;
-          } else if (c <= a.eps) {
-            st.status = kConverged; stop = 1;
-          } else if (it + 1 >= a.max_iters) {
-            st.status = kMaxIter; stop = 1;
-          } else {
-            int take = 0;
-            if (a.accel) {
-              if (a.mask && it < a.mask_len) take = a.mask[(int64_t)j * a.mask_len + it] != 0;
-              else take = c <= a.eta * a.cprev[j];
-            }
-            if (take) {
-              const double al = a.alpha[j];
-              const double an = 0.5 + 0.5 * sqrt(1.0 + 4.0 * al * al);
-              a.coef[j] = (al - 1.0) / an;
-              a.alpha[j] = an;
-              if (al != 1.0) st.momentum += 1;
-            } else {
-              a.alpha[j] = 1.0;
-              a.coef[j] = 0.0;
-            }
-            a.cprev[j] = c;
-          }
-          if (stop) {
-            a.stop[j] = 1;
-            a.base[j] = (a.base[j] + it + 1) % 3;  // the buffer holding the final iterate
-            atomicSub(&ctl->active, 1);
-            atomicExch(&ctl->stopped, 1);
-          }
-        }
+        ls::finish_item(a, j, it, part);
       }
     }
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
-    if (!grid_sync(ctl, nblocks, &sOk)) break;
+    if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
-    // Remove the items of instances that stopped in this iteration from the queue.
-    if (*(volatile int *)&ctl->stopped) {
-      const int src = cl, dst = cl ^ 1;
-      for (int b0 = blockIdx.x * nthreads; b0 < nact; b0 += nblocks * nthreads) {
-        const int qi = b0 + tid;
-        int keep = 0, item = 0;
-        if (qi < nact) {
-          item = a.list[src][qi];
-          keep = *(volatile int *)&a.stop[a.item_inst[item]] == 0;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        int wbase = 0;
-        if ((tid & 31) == 0 && m) wbase = atomicAdd(&ctl->nlist[dst], __popc(m));
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        if (keep) a.list[dst][wbase + __popc(m & ((1u << (tid & 31)) - 1u))] = item;
-      }
-      if (!grid_sync(ctl, nblocks, &sOk)) break;
-      cl = dst;
-      if (blockIdx.x == 0 && tid == 0) {
-        ctl->nlist[src] = 0;
-        ctl->stopped = 0;
-      }
-      if (!grid_sync(ctl, nblocks, &sOk)) break;
-    }
+    if (!ls::compact(a, cl, nact, &sOk)) break;
     (void)ok;
   }
   // Never leave a bulk copy in flight into shared memory: wait (bounded) for pending phases.
@@ -574,93 +457,6 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
     }
 }
 
-// One thread per instance (and per item): reset the per-instance state before a solve.
-template <typename T>
-__global__ void solve_init_kernel(Args<T> a, int warm) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < a.L.batch) {
-    if (warm == 2) a.base[j] = (a.base[j] + 1) % 3;  // the shifted copy is written there
-    a.alpha[j] = 1.0;
-    a.cprev[j] = 1.0;
-    a.coef[j] = 0.0;
-    a.cacc[j] = 0.0;
-    a.ndone[j] = 0;
-    a.stop[j] = a.max_iters <= 0 ? 1 : 0;
-    InstState s;
-    s.iters = 0; s.status = kMaxIter; s.momentum = 0; s.pad = 0; s.c = 0.0;
-    a.st[j] = s;
-  }
-  if (j < a.nitems) a.list[0][j] = j;
-}
-
-// Starting iterates: zero (cold start) or the previous solve's iterates shifted by one stage.
-template <typename T>
-__global__ void prepare_kernel(Args<T> a, int warm, const int *old_base) {
-  const int j = blockIdx.y;
-  const int n = a.L.nx[j] + a.L.nu[j], N = a.L.N[j];
-  const int n5p = iter_stride(n, (int)sizeof(T));
-  const int64_t ib = a.L.Ni[j];
-  T *dst = a.it[a.base[j]] + ib;
-  const T *src = a.it[old_base[j]] + ib;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n5p;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    if (warm == 0) {
-      dst[t] = (T)0;
-    } else {
-      const int k = (int)(t / n5p), r = (int)(t - (int64_t)k * n5p);
-      const int ks = k + 1 < N ? k + 1 : N - 1;
-      dst[t] = src[(int64_t)ks * n5p + r];
-    }
-  }
-}
-
-// u_k and x_{k+1} from z_{k+1} of the final iterate; instances the launch did not finish (a
-// timed-out wait) are reported as PIMPC_TIMEOUT.
-template <typename T>
-__global__ void output_kernel(Args<T> a, double *u_out, double *x_out) {
-  const int j = blockIdx.y;
-  const int nx = a.L.nx[j], nu = a.L.nu[j], n = nx + nu, N = a.L.N[j];
-  const int n5p = iter_stride(n, (int)sizeof(T));
-  if (blockIdx.x == 0 && threadIdx.x == 0 && !a.stop[j]) a.st[j].status = kTimeout;
-  const T *z = a.it[a.base[j]] + a.L.Ni[j];
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
-    const double v = (double)z[(int64_t)k * n5p + c];
-    if (c < nx) {
-      if (x_out) x_out[a.L.Nnx[j] + (int64_t)k * nx + c] = v;
-    } else if (u_out) {
-      u_out[a.L.Nnu[j] + (int64_t)k * nu + (c - nx)] = v;
-    }
-  }
-}
-
-template <typename T>
-Args<T> make_args(const AdmmLaunch &s) {
-  Args<T> a;
-  a.L = s.L;
-  a.blk = (const T *)s.blk;
-  for (int b = 0; b < 3; ++b) a.it[b] = (T *)s.it[b];
-  a.qd = (const T *)s.qd;
-  a.ref = (const T *)s.ref;
-  a.ref_per_stage = s.ref_per_stage;
-  a.lo = (const T *)s.lo;
-  a.hi = (const T *)s.hi;
-  a.xb0 = (const T *)s.xb0;
-  a.rho = s.rho; a.eps = s.eps; a.eta = s.eta;
-  a.max_iters = s.max_iters; a.accel = s.accel;
-  a.mask = s.mask; a.mask_len = s.mask_len;
-  a.item_inst = s.item_inst; a.item_a = s.item_a; a.item_b = s.item_b;
-  a.nitems = s.nitems; a.nitems_inst = s.nitems_inst;
-  a.list[0] = s.list0; a.list[1] = s.list1;
-  a.ctl = s.ctl;
-  a.base = s.base; a.st = s.st;
-  a.alpha = s.alpha; a.cprev = s.cprev; a.coef = s.coef; a.cacc = s.cacc;
-  a.ndone = s.ndone; a.stop = s.stop;
-  a.capI = 0;
-  return a;
-}
-
 template <typename T>
 Smem layout_of(const AdmmLaunch &s) {
   return smem_layout(s.capB, s.capI, s.haloB, s.haloI, s.S_max, s.nv_max, (int)sizeof(T));
@@ -668,33 +464,12 @@ Smem layout_of(const AdmmLaunch &s) {
 
 template <typename T>
 cudaError_t launch_t(const AdmmLaunch &s, cudaStream_t stream) {
-  Args<T> a = make_args<T>(s);
+  Args<T> a = ls::make_args<T>(s);
   Smem lay = layout_of<T>(s);
   a.capI = lay.capI;
-  cudaError_t rc = cudaMemsetAsync(s.ctl, 0, sizeof(Ctl), stream);
-  if (rc != cudaSuccess) return rc;
-  rc = cudaMemcpyAsync(s.old_base, s.base, sizeof(int) * s.L.batch, cudaMemcpyDeviceToDevice, stream);
-  if (rc != cudaSuccess) return rc;
-  const int n_init = std::max(s.L.batch, s.nitems);
-  solve_init_kernel<T><<<(n_init + 255) / 256, 256, 0, stream>>>(a, s.warm);
-  if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
-  if (s.warm != 1) {
-    prepare_kernel<T><<<dim3(8, s.L.batch), 256, 0, stream>>>(a, s.warm, s.old_base);
-    if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
-  }
-  set_control_kernel<<<1, 1, 0, stream>>>(s.ctl, s.nitems, s.L.batch);
-  if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
-  if (s.max_iters > 0) {
-    rc = cudaFuncSetAttribute(admm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)((size_t)lay.total * sizeof(T)));
-    if (rc != cudaSuccess) return rc;
-    void *params[] = {&a, &lay};
-    rc = cudaLaunchCooperativeKernel((const void *)admm_kernel<T>, dim3(s.grid), dim3(s.threads),
-                                     params, (size_t)lay.total * sizeof(T), stream);
-    if (rc != cudaSuccess) return rc;
-  }
-  output_kernel<T><<<dim3(4, s.L.batch), 256, 0, stream>>>(a, s.u_out, s.x_out);
-  return cudaGetLastError();
+  void *params[] = {&a, &lay};
+  return ls::launch_sequence<T>(s, a, (const void *)admm_kernel<T>, params,
+                                (size_t)lay.total * sizeof(T), stream);
 }
 
 }  // namespace

@@ -114,7 +114,13 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   s->device = device; s->batch = batch; s->lti = lti; s->prec = precision;
   s->nx.assign(nx, nx + batch); s->nu.assign(nu, nu + batch); s->N.assign(N, N + batch);
   auto grow = [&](std::vector<int64_t> &v, int64_t &tot, int64_t add) { v.push_back(tot); tot += add; };
-  const int threads = admm_threads(precision);
+  // Instances with n <= 32 use the one-thread-per-stage kernel on the 32-stage tiled layout;
+  // stage-invariant batches with a larger instance use the lane-group kernel on plain blocks.
+  int nmax_batch = 0;
+  for (int j = 0; j < batch; ++j) nmax_batch = std::max(nmax_batch, nx[j] + nu[j]);
+  const int tiled = nmax_batch <= PIMPC_MAX_N_LTV ? 1 : 0;
+  s->tiled = tiled;
+  const int threads = tiled ? tps_threads() : admm_threads(precision);
   const size_t ts = tsize(precision);
   int S_max = 1, nv_max = 2, W_max = 4, n5p_max = 4;
   int64_t capB = 0, capI = 0;
@@ -122,26 +128,29 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   for (int j = 0; j < batch; ++j) {
     const int n = nx[j] + nu[j];
     const int n5p = admm_iter_stride(n, precision);
+    const int64_t ntiles = (N[j] + 31) / 32;
     grow(s->off_nx, s->tot_nx, nx[j]);
     grow(s->off_nu, s->tot_nu, nu[j]);
     grow(s->off_n, s->tot_n, n);
     grow(s->Nnx, s->tot_Nnx, (int64_t)N[j] * nx[j]);
     grow(s->Nnu, s->tot_Nnu, (int64_t)N[j] * nu[j]);
     grow(s->Nn, s->tot_Nn, (int64_t)N[j] * n);
-    grow(s->Ni, s->tot_Ni, (int64_t)N[j] * n5p);
+    grow(s->Ni, s->tot_Ni, tiled ? ntiles * 32 * 5 * n : (int64_t)N[j] * n5p);
     const int64_t reps = lti ? 1 : N[j];
     grow(s->offA, s->tot_A, reps * nx[j] * nx[j]);
     grow(s->offB, s->tot_B, reps * nx[j] * nu[j]);
     grow(s->offe, s->tot_e, reps * nx[j]);
-    const int w = block_words(nx[j], nu[j]);
+    const int w = tiled ? nx[j] * n + nx[j] + n * (n + 1) / 2 + nu[j] * (nu[j] + 1) / 2
+                        : block_words(nx[j], nu[j]);
     s->W.push_back(w);
-    grow(s->blk, s->tot_blk, (int64_t)blocks_per_instance(lti, N[j]) * w);
+    const int64_t blk_words = (tiled && !lti) ? ntiles * 32 * w : (int64_t)blocks_per_instance(lti, N[j]) * w;
+    grow(s->blk, s->tot_blk, (blk_words + 31) / 32 * 32);
     s->stage0.push_back(stage_acc);
     stage_acc += N[j];
     grow(s->bbase, s->nblocks, blocks_per_instance(lti, N[j]));
     s->max_nx = std::max(s->max_nx, nx[j]);
     s->max_n = std::max(s->max_n, n);
-    const int S = threads / admm_group_size(n);
+    const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
     S_max = std::max(S_max, S);
     nv_max = std::max(nv_max, (n + 1) & ~1);
     W_max = std::max(W_max, w);
@@ -151,14 +160,19 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   }
   // Shared-memory plan of the persistent solve kernel.
   AdmmLaunch &P = s->plan;
-  P.capB = (int)capB;
-  P.capI = (int)capI;
-  P.haloB = lti ? 2 * W_max : W_max;
-  P.haloI = 2 * n5p_max;
-  P.S_max = S_max;
-  P.nv_max = nv_max;
   P.threads = threads;
-  s->smem_admm = admm_smem_bytes(P, precision);
+  if (tiled) {
+    P.nv_max = s->max_n;
+    s->smem_admm = tps_smem_bytes(s->max_n, precision);
+  } else {
+    P.capB = (int)capB;
+    P.capI = (int)capI;
+    P.haloB = lti ? 2 * W_max : W_max;
+    P.haloI = 2 * n5p_max;
+    P.S_max = S_max;
+    P.nv_max = nv_max;
+    s->smem_admm = admm_smem_bytes(P, precision);
+  }
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (s->smem_admm + 1024 > (size_t)optin) {
@@ -174,12 +188,13 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   for (int j = 0; j < batch; ++j) {
     const int n = nx[j] + nu[j];
     cost[j] = (double)N[j] * ((lti ? 0 : s->W[j]) + 15.0 * n);
-    const int S = threads / admm_group_size(n);
+    const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
     total_sub += (N[j] + S - 1) / S;
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   int bps = 0, nsm = 0;
-  cudaError_t e = admm_configure(precision, s->smem_admm, &bps);
+  cudaError_t e = tiled ? tps_configure(precision, s->smem_admm, &bps)
+                        : admm_configure(precision, s->smem_admm, &bps);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess || bps < 1) {
     g_create_error = std::string("kernel configuration failed: ") +
@@ -195,9 +210,9 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   for (int oi = 0; oi < batch; ++oi) {
     const int j = order[oi];
     const int n = nx[j] + nu[j];
-    const int S = threads / admm_group_size(n);
+    const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
     int is = (int)(S * m);
-    if (lti) is = std::max(is, std::min(N[j], (256 + S - 1) / S * S));
+    if (lti && !tiled) is = std::max(is, std::min(N[j], (256 + S - 1) / S * S));
     for (int a0 = 0; a0 < N[j]; a0 += is) {
       item_inst.push_back(j);
       item_a.push_back(a0);
@@ -290,6 +305,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(cudaMemset(s->qd64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->rdu64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->qd_T, 0, ts * s->tot_n));
+  chk(cudaMemset(s->blk_T, 0, ts * s->tot_blk));
   for (int b = 0; b < 3; ++b) chk(cudaMemset(s->it[b], 0, ts * s->tot_Ni));
   chk(cudaMemset(s->base, 0, sizeof(int) * batch));
   chk(cudaMemset(s->ferr, 0, sizeof(int) * 4));
@@ -314,6 +330,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   L.Nnx = d_off[3]; L.Nnu = d_off[4]; L.Nn = d_off[5];
   L.offA = d_off[6]; L.offB = d_off[7]; L.offe = d_off[8];
   L.blk = d_off[9]; L.W = d_W; L.stage0 = d_off[10]; L.Ni = d_off[12];
+  L.tiled = tiled;
   *out = s;
   return PIMPC_OK;
 }
@@ -484,7 +501,7 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
   const bool dev = mem == PIMPC_DEVICE;
   a.u_out = u_out ? (dev ? u_out : s->out_u) : nullptr;
   a.x_out = x_out ? (dev ? x_out : s->out_x) : nullptr;
-  PIMPC_CHECK(s, launch_admm(a, s->prec, st), "solve");
+  PIMPC_CHECK(s, s->tiled ? launch_tps(a, s->prec, st) : launch_admm(a, s->prec, st), "solve");
   s->solved = true;
   s->last_ref_per_stage = ref_per_stage;
   s->last_warm = warm_start;

@@ -4,8 +4,7 @@
 //   K = Qbar + rho I + rho Abar_{k+1}^T Abar_{k+1}   (k < N-1),   K = Qbar + rho I   (k = N-1),
 // where Abar^T Abar = G^T G + diag(0, I_nu) with G = [A | B] (Theorem 2's velocity form), factors
 // K = L L^T (Cholesky) and writes H_k = K^{-1}, obtained column by column from L y = e_c and
-// L^T x = y, stored diagonal by diagonal (the layout the iteration reads with consecutive lanes
-// on consecutive words). It also writes M_k = (B_k^T B_k + I + Wdu / rho)^{-1}, so that the du update of
+// L^T x = y. It also writes M_k = (B_k^T B_k + I + Wdu / rho)^{-1}, so that the du update of
 // Algorithm 1 step 1, J_k (v - beta) with J_k = (Bbar^T Bbar)^{-1} Bbar^T, is
 // M_k (B_k^T (v - beta)_x + (v - beta)_u); and it copies G_k and e_k into the stage block.
 // Outputs are converted to the iteration precision T. LTI instances have two blocks: block 0
@@ -118,11 +117,31 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   chol_inverse(S, X, n, ld, lane, a.err);
 
   const int W = a.L.W[j];
-  T *out = blk + a.L.blk[j] + (int64_t)kb * W;
   const int oE = nx * n, oH = oE + nx, oM = oH + n * (n + 1) / 2;
-  // H_k diagonal by diagonal: diagonal d at d n - d (d - 1) / 2 holds H[i][i + d].
-  for (int d = 0; d < n; ++d)
-    for (int i = lane; i < n - d; i += 32) out[oH + d * n - d * (d - 1) / 2 + i] = (T)X[i * ld + i + d];
+  // Element e of this block: tiled stage-varying data interleaves 32 stages element-major;
+  // everything else is a plain block.
+  T *base;
+  int es;
+  if (a.L.tiled && !lti) {
+    base = blk + a.L.blk[j] + (int64_t)(kb >> 5) * 32 * W + (kb & 31);
+    es = 32;
+  } else {
+    base = blk + a.L.blk[j] + (int64_t)kb * W;
+    es = 1;
+  }
+  auto put = [&](int e, double v) { base[(int64_t)e * es] = (T)v; };
+  // Symmetric matrices: packed lower row-major for the one-thread-per-stage kernel, diagonal by
+  // diagonal (diagonal d at d m - d (d - 1) / 2 holds S[i][i + d]) for the lane-group kernel.
+  auto put_sym = [&](int o, int m, const double *Xs, int ld) {
+    if (a.L.tiled) {
+      for (int i = 0; i < m; ++i)
+        for (int c = lane; c <= i; c += 32) put(o + i * (i + 1) / 2 + c, Xs[i * ld + c]);
+    } else {
+      for (int d = 0; d < m; ++d)
+        for (int i = lane; i < m - d; i += 32) put(o + d * m - d * (d - 1) / 2 + i, Xs[i * ld + i + d]);
+    }
+  };
+  put_sym(oH, n, X, ld);
   __syncwarp();
 
   // Own-stage G_k, e_k and M_k = (B_k^T B_k + I + Wdu/rho)^{-1}.
@@ -131,9 +150,9 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     int r = w / n, c = w - r * n;
     double g = c < nx ? Ak[r * nx + c] : Bk[r * nu + (c - nx)];
     G[w] = g;
-    out[w] = (T)g;
+    put(w, g);
   }
-  for (int r = lane; r < nx; r += 32) out[oE + r] = (T)(e ? e[(size_t)kS * nx + r] : 0.0);
+  for (int r = lane; r < nx; r += 32) put(oE + r, e ? e[(size_t)kS * nx + r] : 0.0);
   __syncwarp();
   const double *rdu = a.rdu ? a.rdu + a.L.off_n[j] + nx : nullptr;
   for (int i = 0; i < nu; ++i)
@@ -144,9 +163,8 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
       S[i * nu + c] = s;
     }
   chol_inverse(S, X, nu, nu, lane, a.err);
-  for (int d = 0; d < nu; ++d)
-    for (int i = lane; i < nu - d; i += 32) out[oM + d * nu - d * (d - 1) / 2 + i] = (T)X[i * nu + i + d];
-  for (int w = oM + nu * (nu + 1) / 2 + lane; w < W; w += 32) out[w] = (T)0;
+  put_sym(oM, nu, X, nu);
+  for (int w = oM + nu * (nu + 1) / 2 + lane; w < W; w += 32) put(w, 0.0);
 }
 
 }  // namespace

@@ -46,6 +46,13 @@ size_t admm_smem_bytes(const AdmmLaunch &s, int precision);
 cudaError_t admm_configure(int precision, size_t smem, int *blocks_per_sm);
 cudaError_t launch_admm(const AdmmLaunch &a, int precision, cudaStream_t stream);
 
+// One-thread-per-stage solve (tiled layout, n <= 32).
+int tps_threads();
+int tps_stages_per_subchunk();
+size_t tps_smem_bytes(int nn_max, int precision);
+cudaError_t tps_configure(int precision, size_t smem, int *blocks_per_sm);
+cudaError_t launch_tps(const AdmmLaunch &a, int precision, cudaStream_t stream);
+
 // Elementwise helpers.
 cudaError_t launch_gather_n(const Layout &L, const double *xpart, const double *upart,
                             int64_t total_n, int precision, void *dst, cudaStream_t stream);

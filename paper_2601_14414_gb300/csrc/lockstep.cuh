@@ -1,0 +1,281 @@
+// lockstep.cuh -- the persistent, lock-step frame shared by the solve kernels (internal).
+//
+// One cooperative launch runs every iteration of every instance. In iteration i each CTA pulls
+// work items (instance j, stage range) from a queue and runs the iteration on them; a bounded
+// grid barrier separates iterations. The CTA that finishes the last item of an instance applies
+// Algorithm 1 steps 5-7 for it (stop test, momentum or restart); stopped instances leave the
+// queue by stream compaction after the barrier.
+#pragma once
+#include <math.h>
+
+#include "launch.h"
+
+namespace pimpc {
+namespace ls {
+
+constexpr long long kWaitLimit = 1ll << 22;  // bounded polls of the grid barrier / mbarriers
+
+template <typename T>
+struct Args {
+  Layout L;
+  const T *blk;
+  T *it[3];
+  const T *qd, *ref;
+  int ref_per_stage;
+  const T *lo, *hi, *xb0;
+  double rho, eps, eta;
+  int max_iters, accel;
+  const unsigned char *mask;
+  int mask_len;
+  const int *item_inst, *item_a, *item_b;
+  int nitems;
+  const int *nitems_inst;
+  int *list[2];
+  Ctl *ctl;
+  int *base;
+  InstState *st;
+  double *alpha, *cprev, *coef, *cacc;
+  int *ndone, *stop;
+  int capI;
+};
+
+// Iterate element (vector b in {z, v, theta, beta, lambda}, component c) of stage k.
+// Plain layout: stage-major with stride n5p. Tiled layout: tiles of 32 stages, element-major
+// inside a tile (one 128-byte line per element for 32 stages in FP32).
+__host__ __device__ inline int64_t iter_index(int tiled, int n, int n5p, int k, int b, int c) {
+  if (tiled) return (int64_t)(k >> 5) * (32 * 5 * n) + (int64_t)(b * n + c) * 32 + (k & 31);
+  return (int64_t)k * n5p + b * n + c;
+}
+
+__host__ __device__ inline int iter_stride_plain(int n, int tsize) {
+  const int q = 16 / tsize;
+  return (5 * n + q - 1) / q * q;
+}
+
+// Bounded grid barrier; all CTAs of the cooperative launch are co-resident.
+__device__ inline bool grid_sync(Ctl *c, unsigned nblocks, int *sOk) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = &c->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      c->bar_count = 0;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      long long k = 0;
+      while (*gen == g) {
+        if (++k > kWaitLimit || *(volatile int *)&c->err) { ok = 0; break; }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (!ok) atomicExch(&c->err, 1);
+    *sOk = ok && (*(volatile int *)&c->err == 0);
+  }
+  __syncthreads();
+  return *sOk != 0;
+}
+
+// Step 4's reduction is finished by the caller; this adds the item's share of c^{i+1} and, for
+// the instance's last item of the iteration, applies steps 5-7. Called by one thread.
+template <typename T>
+__device__ inline void finish_item(const Args<T> &a, int j, int it, double part) {
+  atomicAdd(&a.cacc[j], part);
+  __threadfence();
+  const int done = atomicAdd(&a.ndone[j], 1);
+  if (done != a.nitems_inst[j] - 1) return;
+  __threadfence();
+  const double s = __longlong_as_double((long long)atomicExch((unsigned long long *)&a.cacc[j], 0ull));
+  a.ndone[j] = 0;
+  const double c = a.rho * s;
+  InstState &st = a.st[j];
+  st.iters = it + 1;
+  st.c = c;
+  int stop = 0;
+  if (!isfinite(c)) {
+    st.status = kNonFinite; stop = 1;
+  } else if (c <= a.eps) {
+    st.status = kConverged; stop = 1;
+  } else if (it + 1 >= a.max_iters) {
+    st.status = kMaxIter; stop = 1;
+  } else {
+    int take = 0;
+    if (a.accel) {
+      if (a.mask && it < a.mask_len) take = a.mask[(int64_t)j * a.mask_len + it] != 0;
+      else take = c <= a.eta * a.cprev[j];
+    }
+    if (take) {
+      const double al = a.alpha[j];
+      const double an = 0.5 + 0.5 * sqrt(1.0 + 4.0 * al * al);
+      a.coef[j] = (al - 1.0) / an;
+      a.alpha[j] = an;
+      if (al != 1.0) st.momentum += 1;
+    } else {
+      a.alpha[j] = 1.0;
+      a.coef[j] = 0.0;
+    }
+    a.cprev[j] = c;
+  }
+  if (stop) {
+    a.stop[j] = 1;
+    a.base[j] = (a.base[j] + it + 1) % 3;  // the buffer holding the final iterate
+    atomicSub(&a.ctl->active, 1);
+    atomicExch(&a.ctl->stopped, 1);
+  }
+}
+
+// After the iteration barrier: drop the items of stopped instances from the active list.
+// Returns false if a barrier failed. Uniform control flow across the grid.
+template <typename T>
+__device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk) {
+  Ctl *ctl = a.ctl;
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  const unsigned nblocks = gridDim.x;
+  if (!*(volatile int *)&ctl->stopped) return true;
+  const int src = cl, dst = cl ^ 1;
+  for (int b0 = blockIdx.x * nthreads; b0 < nact; b0 += nblocks * nthreads) {
+    const int qi = b0 + tid;
+    int keep = 0, item = 0;
+    if (qi < nact) {
+      item = a.list[src][qi];
+      keep = *(volatile int *)&a.stop[a.item_inst[item]] == 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    int wbase = 0;
+    if ((tid & 31) == 0 && m) wbase = atomicAdd(&ctl->nlist[dst], __popc(m));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (keep) a.list[dst][wbase + __popc(m & ((1u << (tid & 31)) - 1u))] = item;
+  }
+  if (!grid_sync(ctl, nblocks, sOk)) return false;
+  cl = dst;
+  if (blockIdx.x == 0 && tid == 0) {
+    ctl->nlist[src] = 0;
+    ctl->stopped = 0;
+  }
+  return grid_sync(ctl, nblocks, sOk);
+}
+
+// One thread per instance (and per item): reset the per-instance state before a solve.
+template <typename T>
+__global__ void solve_init_kernel(Args<T> a, int warm) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.L.batch) {
+    if (warm == 2) a.base[j] = (a.base[j] + 1) % 3;  // the shifted copy is written there
+    a.alpha[j] = 1.0;
+    a.cprev[j] = 1.0;
+    a.coef[j] = 0.0;
+    a.cacc[j] = 0.0;
+    a.ndone[j] = 0;
+    a.stop[j] = a.max_iters <= 0 ? 1 : 0;
+    InstState s;
+    s.iters = 0; s.status = kMaxIter; s.momentum = 0; s.pad = 0; s.c = 0.0;
+    a.st[j] = s;
+  }
+  if (j < a.nitems) a.list[0][j] = j;
+}
+
+// Starting iterates: zero (cold start) or the previous solve's iterates shifted one stage.
+template <typename T>
+__global__ void prepare_kernel(Args<T> a, int warm, const int *old_base) {
+  const int j = blockIdx.y;
+  const int n = a.L.nx[j] + a.L.nu[j], N = a.L.N[j];
+  const int tiled = a.L.tiled;
+  const int n5p = iter_stride_plain(n, (int)sizeof(T));
+  const int64_t ib = a.L.Ni[j];
+  T *dst = a.it[a.base[j]] + ib;
+  const T *src = a.it[old_base[j]] + ib;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * 5 * n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / (5 * n)), r = (int)(t - (int64_t)k * 5 * n);
+    const int b = r / n, c = r - b * n;
+    const int64_t o = iter_index(tiled, n, n5p, k, b, c);
+    if (warm == 0) {
+      dst[o] = (T)0;
+    } else {
+      const int ks = k + 1 < N ? k + 1 : N - 1;
+      dst[o] = src[iter_index(tiled, n, n5p, ks, b, c)];
+    }
+  }
+}
+
+// u_k and x_{k+1} from z_{k+1} of the final iterate; instances the launch did not finish (a
+// timed-out wait) are reported as PIMPC_TIMEOUT.
+template <typename T>
+__global__ void output_kernel(Args<T> a, double *u_out, double *x_out) {
+  const int j = blockIdx.y;
+  const int nx = a.L.nx[j], nu = a.L.nu[j], n = nx + nu, N = a.L.N[j];
+  const int n5p = iter_stride_plain(n, (int)sizeof(T));
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !a.stop[j]) a.st[j].status = kTimeout;
+  const T *z = a.it[a.base[j]] + a.L.Ni[j];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
+    const double v = (double)z[iter_index(a.L.tiled, n, n5p, k, 0, c)];
+    if (c < nx) {
+      if (x_out) x_out[a.L.Nnx[j] + (int64_t)k * nx + c] = v;
+    } else if (u_out) {
+      u_out[a.L.Nnu[j] + (int64_t)k * nu + (c - nx)] = v;
+    }
+  }
+}
+
+template <typename T>
+Args<T> make_args(const AdmmLaunch &s) {
+  Args<T> a;
+  a.L = s.L;
+  a.blk = (const T *)s.blk;
+  for (int b = 0; b < 3; ++b) a.it[b] = (T *)s.it[b];
+  a.qd = (const T *)s.qd;
+  a.ref = (const T *)s.ref;
+  a.ref_per_stage = s.ref_per_stage;
+  a.lo = (const T *)s.lo;
+  a.hi = (const T *)s.hi;
+  a.xb0 = (const T *)s.xb0;
+  a.rho = s.rho; a.eps = s.eps; a.eta = s.eta;
+  a.max_iters = s.max_iters; a.accel = s.accel;
+  a.mask = s.mask; a.mask_len = s.mask_len;
+  a.item_inst = s.item_inst; a.item_a = s.item_a; a.item_b = s.item_b;
+  a.nitems = s.nitems; a.nitems_inst = s.nitems_inst;
+  a.list[0] = s.list0; a.list[1] = s.list1;
+  a.ctl = s.ctl;
+  a.base = s.base; a.st = s.st;
+  a.alpha = s.alpha; a.cprev = s.cprev; a.coef = s.coef; a.cacc = s.cacc;
+  a.ndone = s.ndone; a.stop = s.stop;
+  a.capI = 0;
+  return a;
+}
+
+// The launch sequence of one solve: per-instance reset, starting iterates, the persistent
+// kernel (cooperative), outputs.
+template <typename T>
+cudaError_t launch_sequence(const AdmmLaunch &s, Args<T> &a, const void *kernel, void **params,
+                            size_t smem, cudaStream_t stream) {
+  cudaError_t rc = cudaMemsetAsync(s.ctl, 0, sizeof(Ctl), stream);
+  if (rc != cudaSuccess) return rc;
+  rc = cudaMemcpyAsync(s.old_base, s.base, sizeof(int) * s.L.batch, cudaMemcpyDeviceToDevice, stream);
+  if (rc != cudaSuccess) return rc;
+  const int n_init = s.L.batch > s.nitems ? s.L.batch : s.nitems;
+  solve_init_kernel<T><<<(n_init + 255) / 256, 256, 0, stream>>>(a, s.warm);
+  if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+  if (s.warm != 1) {
+    prepare_kernel<T><<<dim3(8, s.L.batch), 256, 0, stream>>>(a, s.warm, s.old_base);
+    if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+  }
+  set_control_kernel<<<1, 1, 0, stream>>>(s.ctl, s.nitems, s.L.batch);
+  if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
+  if (s.max_iters > 0) {
+    rc = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (rc != cudaSuccess) return rc;
+    rc = cudaLaunchCooperativeKernel(kernel, dim3(s.grid), dim3(s.threads), params, smem, stream);
+    if (rc != cudaSuccess) return rc;
+  }
+  output_kernel<T><<<dim3(4, s.L.batch), 256, 0, stream>>>(a, s.u_out, s.x_out);
+  return cudaGetLastError();
+}
+
+}  // namespace ls
+}  // namespace pimpc

@@ -1,5 +1,5 @@
 // misc.cu -- elementwise marshalling kernels: FP64 ABI arrays <-> the solver's internal layout.
-#include "launch.h"
+#include "lockstep.cuh"
 
 namespace pimpc {
 
@@ -26,21 +26,21 @@ __global__ void convert_kernel(const double *src, int64_t count, T *dst) {
     dst[i] = (T)src[i];
 }
 
-// Iterates of stage k: [z | v | theta | beta | lambda] (stride n5p) -> five [sum N n] FP64 arrays.
+// Iterates of stage k (vectors z, v, theta, beta, lambda in either layout) -> five [sum N n]
+// FP64 arrays.
 template <typename T>
 __global__ void export_kernel(Layout L, T *it0, T *it1, T *it2, const int *base, double *z,
                               double *v, double *th, double *be, double *la) {
   const int j = blockIdx.x;
   const int n = L.nx[j] + L.nu[j], N = L.N[j];
-  const int q = 16 / (int)sizeof(T);
-  const int n5p = (5 * n + q - 1) / q * q;
+  const int n5p = ls::iter_stride_plain(n, (int)sizeof(T));
   T *bufs[3] = {it0, it1, it2};
   const T *src = bufs[base[j]] + L.Ni[j];
   double *outs[5] = {z, v, th, be, la};
   for (int64_t t = threadIdx.x; t < (int64_t)N * n; t += blockDim.x) {
     const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
     for (int b = 0; b < 5; ++b)
-      if (outs[b]) outs[b][L.Nn[j] + t] = (double)src[(int64_t)k * n5p + b * n + c];
+      if (outs[b]) outs[b][L.Nn[j] + t] = (double)src[ls::iter_index(L.tiled, n, n5p, k, b, c)];
   }
 }
 

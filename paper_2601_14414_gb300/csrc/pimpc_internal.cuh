@@ -31,6 +31,7 @@ constexpr int kMaxNLti = 64;
 struct Layout {
   int batch;
   int lti;
+  int tiled;                       // 1: 32-stage tiled layout (n <= 32); 0: plain stage-major
   const int *nx, *nu, *N;          // [batch]
   const int64_t *off_nx, *off_nu, *off_n;   // per-instance vector offsets
   const int64_t *Nnx, *Nnu, *Nn;   // per-stage array offsets
