@@ -217,6 +217,38 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
                    double *g_ref, double *g_q, double *g_r, double *g_xmin, double *g_xmax,
                    double *g_umin, double *g_umax, int checkpoint_every, int mem, void *stream);
 
+/*
+ * pimpc_solve_static -- one instance, solved without allocating any device memory.
+ *
+ * No counterpart in the paper: this entry point exists for callers that cannot call cudaMalloc
+ * (work recorded into a CUDA graph that must not allocate, real-time loops that forbid
+ * allocation after start-up, hosts whose device allocator belongs to another framework). It
+ * computes what pimpc_create + set_* + pimpc_solve (cold start) compute for a single
+ * stage-varying instance, with the same kernels, but its working memory is one file-scope
+ * device array of PIMPC_STATIC_BYTES that every GPU loading the library holds until exit.
+ *   nx, nu, N     sizes, 1 <= nx, 1 <= nu, nx + nu <= PIMPC_MAX_N_LTV, N >= 1.
+ *   precision     PIMPC_F32 or PIMPC_F64 iterations (factorisation in FP64).
+ *   A [N nx nx], B [N nx nu], e [N nx] (NULL = 0), q [nx], r [nu], xmin, xmax [nx],
+ *   umin, umax [nu], x0 [nx], ref [n] (constant reference, NULL = 0): DEVICE memory, FP64,
+ *   owned by the caller, read during the call's kernels only.
+ *   rho, eps, max_iters, accel, eta  as in pimpc_set_options.
+ *   u_out [N nu], x_out [N nx], iters[1], c[1], status[1]: DEVICE memory (any may be NULL).
+ *   stream        cudaStream_t; the call only enqueues work on it.
+ * The call allocates nothing (no cudaMalloc, no cudaFree, no allocating library call). Its
+ * first call on a device looks up the array's address with cudaGetSymbolAddress; make that
+ * first call before any stream capture. Every call shares the array and rewrites or clears what
+ * it reads, so consecutive calls are independent, but calls that overlap on the GPU race.
+ * Errors: PIMPC_EINVAL (sizes, or an instance whose working memory exceeds PIMPC_STATIC_BYTES;
+ * the message is in pimpc_last_error(NULL)), PIMPC_ECUDA.
+ */
+#define PIMPC_STATIC_BYTES (16u << 20)
+int pimpc_solve_static(int nx, int nu, int N, int precision, const double *A, const double *B,
+                       const double *e, const double *q, const double *r, const double *xmin,
+                       const double *xmax, const double *umin, const double *umax,
+                       const double *x0, const double *ref, double rho, double eps,
+                       int max_iters, int accel, double eta, double *u_out, double *x_out,
+                       int *iters, double *c, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

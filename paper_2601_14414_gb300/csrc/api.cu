@@ -27,6 +27,8 @@ thread_local std::string g_create_error;
 
 namespace pimpc {
 
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+
 int fail(pimpc_solver *s, int code, const std::string &msg) {
   if (s) s->err = msg;
   return code;

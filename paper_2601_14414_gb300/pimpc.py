@@ -47,6 +47,7 @@ _SIGS = {
     "pimpc_set_restart_mask": (_I, [_VP, _VP, _I, _I, _VP]),
     "pimpc_plant_step": (_I, [_VP, _I, _VP, _D, _VP, _VP, _VP, _I, _VP]),
     "pimpc_backward": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP]),
+    "pimpc_solve_static": (_I, [_I, _I, _I, _I] + [_VP] * 11 + [_D, _D, _I, _I, _D] + [_VP] * 6),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -212,6 +213,19 @@ def pimpc_backward(h, dL_du, dL_dx, g_x0=None, g_ref=None, g_q=None, g_r=None, g
                    g_xmax=None, g_umin=None, g_umax=None, checkpoint_every=25):
     p, mem, st = _marshal(dL_du, dL_dx, g_x0, g_ref, g_q, g_r, g_xmin, g_xmax, g_umin, g_umax)
     _check(h, load().pimpc_backward(h, *p, int(checkpoint_every), mem, st))
+
+
+def pimpc_solve_static(nx, nu, N, precision, A, B, e, q, r, xmin, xmax, umin, umax, x0, ref,
+                       rho, eps, max_iters, accel, eta, u_out=None, x_out=None, iters=None,
+                       c=None, status=None):
+    """Single-instance solve that allocates nothing; every array is a CUDA tensor."""
+    p, mem, st = _marshal(A, B, e, q, r, xmin, xmax, umin, umax, x0, ref, u_out, x_out, iters,
+                          c, status)
+    if mem != DEVICE:
+        raise ValueError("pimpc_solve_static takes device arrays only")
+    _check(None, load().pimpc_solve_static(int(nx), int(nu), int(N), int(precision), *p[:11],
+                                           float(rho), float(eps), int(max_iters), int(accel),
+                                           float(eta), *p[11:], st))
 
 
 # ---- packing of per-instance dicts ----------------------------------------------------------
