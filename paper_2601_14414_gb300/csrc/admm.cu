@@ -114,7 +114,7 @@ __host__ __device__ inline Smem smem_layout(int capB, int capI, int haloB, int h
   s.haloI = s.haloB + up(haloB);
   s.scr = s.haloI + up(haloI);
   s.X = s.scr + up(S_max * 4 * nv_max);
-  s.total = s.X + up((S_max + 1) * nv_max);
+  s.total = s.X + up(2 * (S_max + 1) * nv_max);  // xbar rows, double-buffered
   return s;
 }
 
@@ -135,18 +135,56 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, Ctl *c) {
   return true;
 }
 
-// Symmetric m x m matrix stored diagonal by diagonal: diagonal d starts at d m - d (d - 1) / 2 and
-// holds A[i][i + d], i = 0 .. m-1-d.  Returns (A x)_c; consecutive lanes read consecutive words.
+// (S x)_c for a symmetric m x m matrix S stored as wrapped diagonals: row d (d <= m/2) holds
+// S[c][(c + d) mod m]; S[c][(c - d) mod m] = S[(c - d) mod m][c] is entry (c - d) mod m of row d.
+// Consecutive lanes read consecutive words of each row and distinct words of x.
 template <typename T>
-__device__ __forceinline__ T sym_diag_row(const T *D, const T *x, int m, int c) {
+__device__ __forceinline__ T sym_wrapped(const T *D, const T *x, int m, int c) {
   T acc0 = D[c] * x[c], acc1 = (T)0;
-  int off = m;
-  for (int d = 1; d < m; ++d) {
-    if (c + d < m) acc0 += D[off + c] * x[c + d];
-    if (c >= d) acc1 += D[off + c - d] * x[c - d];
-    off += m - d;
+  const int half = (m - 1) / 2;
+  int ip = c, im = c;
+  const T *row = D;
+  for (int d = 1; d <= half; ++d) {
+    row += m;
+    ip = (ip + 1 == m) ? 0 : ip + 1;
+    im = (im == 0) ? m - 1 : im - 1;
+    acc0 += row[c] * x[ip];
+    acc1 += row[im] * x[im];
+  }
+  if ((m & 1) == 0) {
+    row += m;
+    const int jm = c + m / 2 < m ? c + m / 2 : c - m / 2;
+    acc0 += row[c] * x[jm];
   }
   return acc0 + acc1;
+}
+
+// sum_{r < cnt} M[r * ld] * v[r] with v 16-byte aligned in shared memory (read as vectors,
+// identical for every lane of the group, so the reads broadcast).
+template <typename T>
+__device__ __forceinline__ T dot_col(const T *M, int ld, const T *v, int cnt) {
+  T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+  int r = 0;
+  if constexpr (sizeof(T) == 4) {
+    for (; r + 3 < cnt; r += 4) {
+      const float4 q = *reinterpret_cast<const float4 *>(v + r);
+      a0 += M[(r + 0) * ld] * q.x;
+      a1 += M[(r + 1) * ld] * q.y;
+      a2 += M[(r + 2) * ld] * q.z;
+      a3 += M[(r + 3) * ld] * q.w;
+    }
+  } else {
+    for (; r + 3 < cnt; r += 4) {
+      const double2 q0 = *reinterpret_cast<const double2 *>(v + r);
+      const double2 q1 = *reinterpret_cast<const double2 *>(v + r + 2);
+      a0 += M[(r + 0) * ld] * q0.x;
+      a1 += M[(r + 1) * ld] * q0.y;
+      a2 += M[(r + 2) * ld] * q1.x;
+      a3 += M[(r + 3) * ld] * q1.y;
+    }
+  }
+  for (; r < cnt; ++r) a0 += M[r * ld] * v[r];
+  return (a0 + a1) + (a2 + a3);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -189,9 +227,10 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
       if (*(volatile int *)&a.stop[j]) continue;
       const int ka = a.item_a[item], kb = a.item_b[item];
       const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j], n = nx + nu;
-      const int g = group_size(n), S = nthreads / g, nv = (n + 1) & ~1;
+      const int g = group_size(n), S = nthreads / g, nv = (n + 3) & ~3;
       const int n5p = iter_stride(n, (int)sizeof(T));
       const int W = a.L.W[j];
+      const int ldg = odd_ld(n);
       const int bse = a.base[j];
       const int64_t ib = a.L.Ni[j];
       const T *Ic = a.it[(bse + it) % 3] + ib;
@@ -211,10 +250,9 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
       const int ncl = (g == 32 && n > 32) ? 2 : 1;
       T *scr = sm + lay.scr + grp * 4 * nv;
       T *sW = scr, *sY = scr + nv, *sH = scr + 2 * nv, *sDU = scr + 3 * nv;
-      T *X = sm + lay.X;
       T *haloB = sm + lay.haloB, *haloI = sm + lay.haloI;
       const T *ltiB = haloB;  // LTI: block 0 (H_k, k < N-1) then block 1 (H_{N-1})
-      const int oE = nx * n, oH = oE + nx, oM = oH + n * (n + 1) / 2;
+      const int oE = nx * ldg, oH = oE + nx, oM = oH + wrapped_size(n);
       T cacc = (T)0;
 
       // Copies of the sub-chunk that starts at stage k0 into buffer b (thread 0 issues).
@@ -258,17 +296,23 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
           pend[b ^ 1] = true;
         }
         const bool arrived = mbar_wait(&mbar[b], par[b], ctl);
-        if (!__syncthreads_and(arrived)) { ok = false; break; }  // uniform across the CTA
-        par[b] ^= 1u;
-        pend[b] = false;
+        if (arrived) {
+          par[b] ^= 1u;
+          pend[b] = false;
+        } else {
+          ok = false;  // the copy may still be in flight: it stays pending for the exit wait
+        }
         const T *rB = sm + lay.rawB + b * lay.capB;
         const T *rIc = sm + lay.rawI + b * 2 * lay.capI;
         const T *rIp = rIc + lay.capI;
+        // xbar rows: Xc for this sub-chunk; the last stage also seeds row 0 of the next one
+        T *Xc = sm + lay.X + (sc & 1) * (S + 1) * nv;
+        T *Xn = sm + lay.X + ((sc & 1) ^ 1) * (S + 1) * nv;
 
         // ---- phase 1: step 1 ----
         T zh[2], vh[2], thh[2], beh[2], lah[2];
         const int k = k0 + grp;
-        const bool active = grp < cnt;
+        const bool active = arrived && grp < cnt;
         const T *Hk = lti ? (ltiB + ((k < N - 1) ? 0 : W)) : rB + grp * W;  // block holding H_k
         const T *Gk = lti ? ltiB : rB + grp * W;                           // G_k, e_k, M_k
         const T *Gk1 = lti ? ltiB : rB + (grp + 1) * W;                    // G_{k+1}, e_{k+1}
@@ -303,14 +347,9 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
           }
         }
         __syncwarp();
-        if (active && l < nu) {  // t = B_k^T w_x + w_u
-          T t = sW[nx + l];
-          const T *col = Gk + nx + l;
-          for (int r = 0; r < nx; ++r) t += col[r * n] * sW[r];
-          sH[l] = t;
-        }
+        if (active && l < nu) sH[l] = sW[nx + l] + dot_col(Gk + nx + l, ldg, sW, nx);  // B_k^T w_x + w_u
         __syncwarp();
-        if (active && l < nu) sDU[l] = sym_diag_row(Gk + oM, sH, nu, l);  // du_k = M_k t
+        if (active && l < nu) sDU[l] = sym_wrapped(Gk + oM, sH, nu, l);  // du_k = M_k t
         __syncwarp();
         if (active) {
           for (int qq = 0; qq < ncl; ++qq) {
@@ -318,15 +357,7 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
             if (c < n) {
               T acc = (T)0;
               if (k + 1 < N) {  // Abar_{k+1}^T y = G_{k+1}^T y_x + (0, y_u)
-                const T *col = Gk1 + c;
-                T acc1 = (T)0;
-                int r = 0;
-                for (; r + 1 < nx; r += 2) {
-                  acc += col[r * n] * sY[r];
-                  acc1 += col[(r + 1) * n] * sY[r + 1];
-                }
-                if (r < nx) acc += col[r * n] * sY[r];
-                acc += acc1;
+                acc = dot_col(Gk1 + c, ldg, sY, nx);
                 if (c >= nx) acc += sY[c];
               }
               const T rf = ref ? ref[(int64_t)k * refstride + c] : (T)0;
@@ -338,15 +369,19 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
         if (active) {
           for (int qq = 0; qq < ncl; ++qq) {
             const int c = l + 32 * qq;
-            if (c < n) X[(grp + 1) * nv + c] = sym_diag_row(Hk + oH, sH, n, c);  // xbar_{k+1}
+            if (c < n) {
+              const T xn = sym_wrapped(Hk + oH, sH, n, c);  // xbar_{k+1} = H_k h_k
+              Xc[(grp + 1) * nv + c] = xn;
+              if (grp + 1 == cnt) Xn[c] = xn;
+            }
           }
         }
-        // xbar_k of the sub-chunk's first stage: xbar_0, the previous sub-chunk's last result
-        // (already in row 0), or for an item starting at a > 0, H_{a-1} h_{a-1} from the halo.
+        // xbar_k of the first stage: xbar_0, or (first sub-chunk of an item that starts at
+        // a > 0) H_{a-1} h_{a-1} recomputed from the halo; later sub-chunks got it above.
         if (sc == 0) {
           if (ka == 0) {
-            for (int c = tid; c < n; c += nthreads) X[c] = a.xb0[a.L.off_n[j] + c];
-          } else if (grp == 0) {
+            for (int c = tid; c < n; c += nthreads) Xc[c] = a.xb0[a.L.off_n[j] + c];
+          } else if (grp == 0 && arrived) {
             __syncwarp(gmask);
             for (int qq = 0; qq < ncl; ++qq) {  // y_a from this group's own hats (stage a)
               const int c = l + 32 * qq;
@@ -358,9 +393,7 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
             for (int qq = 0; qq < ncl; ++qq) {
               const int c = l + 32 * qq;
               if (c < n) {
-                const T *col = Gk + c;
-                T acc = (T)0;
-                for (int r = 0; r < nx; ++r) acc += col[r * n] * sY[r];
+                T acc = dot_col(Gk + c, ldg, sY, nx);
                 if (c >= nx) acc += sY[c];
                 T zm = hcm[c], tm = hcm[2 * n + c];
                 if (use_prev) {
@@ -374,40 +407,26 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
             __syncwarp(gmask);
             for (int qq = 0; qq < ncl; ++qq) {
               const int c = l + 32 * qq;
-              if (c < n) X[c] = sym_diag_row(Hm + oH, sW, n, c);
+              if (c < n) Xc[c] = sym_wrapped(Hm + oH, sW, n, c);
             }
           }
         }
-        __syncthreads();
+        if (!__syncthreads_and(arrived)) { ok = false; break; }  // uniform across the CTA
 
         // ---- phase 2: steps 2-4 ----
         if (active) {
-          const T *xk = X + grp * nv;
-          const T *xk1 = X + (grp + 1) * nv;
+          const T *xk = Xc + grp * nv;
+          const T *xk1 = Xc + (grp + 1) * nv;
           T *o = In + (int64_t)k * n5p;
           for (int qq = 0; qq < ncl; ++qq) {
             const int c = l + 32 * qq;
             if (c < n) {
               T ax, bd, ee;
               if (c < nx) {
-                // row c of G; the column order is rotated by c so lanes read distinct banks
-                const T *row = Gk + c * n;
-                T s1 = (T)0, s1b = (T)0, s2 = (T)0;
-                int cc = c;
-                int t = 0;
-                for (; t + 1 < n; t += 2) {
-                  s1 += row[cc] * xk[cc];
-                  cc = (cc + 1 == n) ? 0 : cc + 1;
-                  s1b += row[cc] * xk[cc];
-                  cc = (cc + 1 == n) ? 0 : cc + 1;
-                }
-                if (t < n) s1 += row[cc] * xk[cc];
-                int cu = c % nu;
-                for (int t2 = 0; t2 < nu; ++t2) {
-                  s2 += row[nx + cu] * sDU[cu];
-                  cu = (cu + 1 == nu) ? 0 : cu + 1;
-                }
-                ax = s1 + s1b; bd = s2; ee = Gk[oE + c];
+                const T *row = Gk + c * ldg;  // odd stride: the lanes' rows hit distinct banks
+                ax = dot_col(row, 1, xk, n);
+                bd = dot_col(row + nx, 1, sDU, nu);
+                ee = Gk[oE + c];
               } else {
                 ax = xk[c]; bd = sDU[c - nx]; ee = (T)0;
               }
@@ -427,8 +446,6 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
           }
         }
         __syncthreads();
-        for (int c = tid; c < n; c += nthreads) X[c] = X[cnt * nv + c];
-        __syncthreads();
       }
       if (!ok) break;
 
@@ -446,7 +463,6 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk)) break;
-    (void)ok;
   }
   // Never leave a bulk copy in flight into shared memory: wait (bounded) for pending phases.
   for (int b = 0; b < 2; ++b)

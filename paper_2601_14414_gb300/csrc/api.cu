@@ -116,11 +116,9 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   s->device = device; s->batch = batch; s->lti = lti; s->prec = precision;
   s->nx.assign(nx, nx + batch); s->nu.assign(nu, nu + batch); s->N.assign(N, N + batch);
   auto grow = [&](std::vector<int64_t> &v, int64_t &tot, int64_t add) { v.push_back(tot); tot += add; };
-  // Instances with n <= 32 use the one-thread-per-stage kernel on the 32-stage tiled layout;
-  // stage-invariant batches with a larger instance use the lane-group kernel on plain blocks.
-  int nmax_batch = 0;
-  for (int j = 0; j < batch; ++j) nmax_batch = std::max(nmax_batch, nx[j] + nu[j]);
-  const int tiled = nmax_batch <= PIMPC_MAX_N_LTV ? 1 : 0;
+  // The batched solve runs the lane-group kernel on plain stage blocks. (The one-thread-per-stage
+  // kernel on the 32-stage tiled layout serves pimpc_solve_static.)
+  const int tiled = 0;
   s->tiled = tiled;
   const int threads = tiled ? tps_threads() : admm_threads(precision);
   const size_t ts = tsize(precision);
@@ -154,7 +152,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
     s->max_n = std::max(s->max_n, n);
     const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
     S_max = std::max(S_max, S);
-    nv_max = std::max(nv_max, (n + 1) & ~1);
+    nv_max = std::max(nv_max, tiled ? n : (n + 3) & ~3);
     W_max = std::max(W_max, w);
     n5p_max = std::max(n5p_max, n5p);
     if (!lti) capB = std::max<int64_t>(capB, (int64_t)(S + 1) * w);

@@ -117,12 +117,15 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   chol_inverse(S, X, n, ld, lane, a.err);
 
   const int W = a.L.W[j];
-  const int oE = nx * n, oH = oE + nx, oM = oH + n * (n + 1) / 2;
+  const bool tiled = a.L.tiled != 0;
+  const int ldg = tiled ? n : odd_ld(n);
+  const int oE = nx * ldg, oH = oE + nx;
+  const int oM = oH + (tiled ? packed_size(n) : wrapped_size(n));
   // Element e of this block: tiled stage-varying data interleaves 32 stages element-major;
   // everything else is a plain block.
   T *base;
   int es;
-  if (a.L.tiled && !lti) {
+  if (tiled && !lti) {
     base = blk + a.L.blk[j] + (int64_t)(kb >> 5) * 32 * W + (kb & 31);
     es = 32;
   } else {
@@ -130,15 +133,16 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     es = 1;
   }
   auto put = [&](int e, double v) { base[(int64_t)e * es] = (T)v; };
-  // Symmetric matrices: packed lower row-major for the one-thread-per-stage kernel, diagonal by
-  // diagonal (diagonal d at d m - d (d - 1) / 2 holds S[i][i + d]) for the lane-group kernel.
-  auto put_sym = [&](int o, int m, const double *Xs, int ld) {
-    if (a.L.tiled) {
+  // Symmetric matrices: packed lower row-major (one-thread-per-stage kernel) or wrapped
+  // diagonals, row d holding S[c][(c + d) mod m] (lane-group kernel).
+  auto put_sym = [&](int o, int m, const double *Xs, int ldx) {
+    if (tiled) {
       for (int i = 0; i < m; ++i)
-        for (int c = lane; c <= i; c += 32) put(o + i * (i + 1) / 2 + c, Xs[i * ld + c]);
+        for (int c = lane; c <= i; c += 32) put(o + i * (i + 1) / 2 + c, Xs[i * ldx + c]);
     } else {
-      for (int d = 0; d < m; ++d)
-        for (int i = lane; i < m - d; i += 32) put(o + d * m - d * (d - 1) / 2 + i, Xs[i * ld + i + d]);
+      const int rows = wrapped_rows(m);
+      for (int d = 0; d < rows; ++d)
+        for (int c = lane; c < m; c += 32) put(o + d * m + c, Xs[c * ldx + (c + d) % m]);
     }
   };
   put_sym(oH, n, X, ld);
@@ -150,8 +154,10 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     int r = w / n, c = w - r * n;
     double g = c < nx ? Ak[r * nx + c] : Bk[r * nu + (c - nx)];
     G[w] = g;
-    put(w, g);
+    put(r * ldg + c, g);
   }
+  if (ldg > n)
+    for (int r = lane; r < nx; r += 32) put(r * ldg + n, 0.0);
   for (int r = lane; r < nx; r += 32) put(oE + r, e ? e[(size_t)kS * nx + r] : 0.0);
   __syncwarp();
   const double *rdu = a.rdu ? a.rdu + a.L.off_n[j] + nx : nullptr;

@@ -5,12 +5,11 @@
 //   per-stage arrays at Nnx[j] = sum_{i<j} N_i nx_i, Nnu[j], Nn[j] = sum N_i n_i, matrices at
 //   offA[j] (sum N nx^2, or sum nx^2 when lti), offB[j], offe[j].
 //
-// Stage block (iteration precision T), the unit the ADMM kernel streams. For one stage k:
-//   [ G_k = [A_k | B_k] : nx x n row-major ][ e_k : nx ][ H_k : n(n+1)/2 ][ M_k : nu(nu+1)/2 ],
-// padded to a multiple of 4 elements (W words). The symmetric H_k and M_k are stored diagonal by
-// diagonal: diagonal d of an m x m matrix starts at d m - d (d - 1) / 2 and holds A[i][i + d],
-// i = 0 .. m-1-d. An LTV instance has N blocks at blk[j] + k W; an LTI instance has two: block 0
-// (H = H_k, k < N-1) and block 1 (H = H_{N-1}).
+// Stage block (iteration precision T), the unit the solve kernels stream. Plain layout (lane-group
+// kernel): [ G_k = [A_k | B_k] : nx rows of stride odd_ld(n) ][ e_k : nx ][ H_k wrapped
+// diagonals ][ M_k wrapped diagonals ], padded to a multiple of 4 elements (W words); an LTV
+// instance has N blocks at blk[j] + k W, an LTI instance two (H_k for k < N-1, then H_{N-1}).
+// Tiled layout (one-thread-per-stage kernel): see admm_tps.cu.
 //
 // Iterates (T): three rotating buffers it[0..2]; stage k of instance j holds [z | v | theta | beta |
 // lambda] (5 n values, z = z_{k+1}, padded to a 16-byte multiple n5p) at Ni[j] + n5p k. base[j]
@@ -55,9 +54,17 @@ struct Ctl {
 };
 
 __host__ __device__ inline int packed_size(int n) { return n * (n + 1) / 2; }
+// Plain stage block of the lane-group kernel: G rows padded to an odd stride, symmetric H and M
+// as wrapped diagonals (see wrapped_size).
+__host__ __device__ inline int odd_ld(int n) { return n | 1; }
+// Wrapped-diagonal storage of a symmetric m x m matrix S: for d = 0 .. m/2, row d holds
+// S[c][(c + d) mod m] for c = 0 .. m-1. Diagonals d and m-d hold the same elements, so only
+// d <= m/2 is stored: m (1 + floor((m-1)/2) + [m even]) elements.
+__host__ __device__ inline int wrapped_rows(int m) { return 1 + (m - 1) / 2 + ((m % 2 == 0) ? 1 : 0); }
+__host__ __device__ inline int wrapped_size(int m) { return m * wrapped_rows(m); }
 __host__ __device__ inline int block_words(int nx, int nu) {
   int n = nx + nu;
-  int w = nx * n + nx + packed_size(n) + packed_size(nu);
+  int w = nx * odd_ld(n) + nx + wrapped_size(n) + wrapped_size(nu);
   return (w + 3) & ~3;
 }
 __host__ __device__ inline int blocks_per_instance(int lti, int N) { return lti ? 2 : N; }
