@@ -170,7 +170,8 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     }
   chol_inverse(S, X, nu, nu, lane, a.err);
   put_sym(oM, nu, X, nu);
-  for (int w = oM + nu * (nu + 1) / 2 + lane; w < W; w += 32) put(w, 0.0);
+  const int end = oM + (tiled ? packed_size(nu) : wrapped_size(nu));
+  for (int w = end + lane; w < W; w += 32) put(w, 0.0);
 }
 
 }  // namespace
