@@ -98,23 +98,26 @@ __host__ __device__ inline int iter_stride(int n, int tsize) {
 
 // Shared-memory layout of a launch (sized by the largest instance of the batch), in elements.
 struct Smem {
-  int rawB, capB, rawI, capI, haloB, haloI, scr, X, total;
+  int nbuf, rawB, capB, rawI, capI, haloB, haloI, scr, X, total;
 };
 
+// nbuf = 2: the copies of sub-chunk s+1 overlap the compute of sub-chunk s inside the CTA;
+// nbuf = 1: one buffer, and the overlap comes from the other CTAs resident on the SM.
 __host__ __device__ inline Smem smem_layout(int capB, int capI, int haloB, int haloI, int S_max,
-                                            int nv_max, int tsize) {
+                                            int nv_max, int tsize, int nbuf) {
   const int q = 16 / tsize;
   auto up = [q](int v) { return (v + q - 1) / q * q; };
   Smem s;
+  s.nbuf = nbuf;
   s.capB = up(capB);
   s.capI = up(capI);
   s.rawB = 0;
-  s.rawI = s.rawB + 2 * s.capB;
-  s.haloB = s.rawI + 4 * s.capI;  // two buffers x (cur, prev)
+  s.rawI = s.rawB + nbuf * s.capB;
+  s.haloB = s.rawI + 2 * nbuf * s.capI;  // per buffer: cur, then prev
   s.haloI = s.haloB + up(haloB);
   s.scr = s.haloI + up(haloI);
-  s.X = s.scr + up(S_max * 4 * nv_max);
-  s.total = s.X + up(2 * (S_max + 1) * nv_max);  // xbar rows, double-buffered
+  s.X = s.scr + up(S_max);         // S_max here carries max_j S_j * 4 * nv_j (group scratch)
+  s.total = s.X + up(nv_max);       // nv_max here carries max_j 2 (S_j + 1) nv_j (xbar rows)
   return s;
 }
 
@@ -288,12 +291,15 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
       if (tid == 0) issue(ka, 0, true);
       pend[0] = true;
       int b = 0;
-      for (int sc = 0; sc < nsub; ++sc, b ^= 1) {
+      for (int sc = 0; sc < nsub; ++sc, b ^= (lay.nbuf - 1)) {
         const int k0 = ka + sc * S;
         const int cnt = min(S, kb - k0);
-        if (sc + 1 < nsub) {
+        if (lay.nbuf == 2 && sc + 1 < nsub) {
           if (tid == 0) issue(k0 + S, b ^ 1, false);
           pend[b ^ 1] = true;
+        } else if (lay.nbuf == 1 && sc > 0) {
+          if (tid == 0) issue(k0, 0, false);  // the single buffer is free after the last barrier
+          pend[0] = true;
         }
         const bool arrived = mbar_wait(&mbar[b], par[b], ctl);
         if (arrived) {
@@ -475,7 +481,7 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
 
 template <typename T>
 Smem layout_of(const AdmmLaunch &s) {
-  return smem_layout(s.capB, s.capI, s.haloB, s.haloI, s.S_max, s.nv_max, (int)sizeof(T));
+  return smem_layout(s.capB, s.capI, s.haloB, s.haloI, s.S_max, s.nv_max, (int)sizeof(T), s.nbuf);
 }
 
 template <typename T>

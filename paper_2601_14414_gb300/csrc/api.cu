@@ -122,7 +122,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   s->tiled = tiled;
   const int threads = tiled ? tps_threads() : admm_threads(precision);
   const size_t ts = tsize(precision);
-  int S_max = 1, nv_max = 2, W_max = 4, n5p_max = 4;
+  int S_max = 1, nv_max = 2, W_max = 4, n5p_max = 4, scr_max = 4, xrows_max = 4;
   int64_t capB = 0, capI = 0;
   int64_t stage_acc = 0;
   for (int j = 0; j < batch; ++j) {
@@ -151,8 +151,11 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
     s->max_nx = std::max(s->max_nx, nx[j]);
     s->max_n = std::max(s->max_n, n);
     const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
+    const int nv = (n + 3) & ~3;
+    scr_max = std::max(scr_max, S * 4 * nv);        // per-group scratch rows
+    xrows_max = std::max(xrows_max, 2 * (S + 1) * nv);  // double-buffered xbar rows
     S_max = std::max(S_max, S);
-    nv_max = std::max(nv_max, tiled ? n : (n + 3) & ~3);
+    nv_max = std::max(nv_max, tiled ? n : nv);
     W_max = std::max(W_max, w);
     n5p_max = std::max(n5p_max, n5p);
     if (!lti) capB = std::max<int64_t>(capB, (int64_t)(S + 1) * w);
@@ -169,8 +172,9 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
     P.capI = (int)capI;
     P.haloB = lti ? 2 * W_max : W_max;
     P.haloI = 2 * n5p_max;
-    P.S_max = S_max;
-    P.nv_max = nv_max;
+    P.S_max = scr_max;    // the lane-group kernel's plan takes the scratch and xbar-row sizes
+    P.nv_max = xrows_max;
+    P.nbuf = 1;
     s->smem_admm = admm_smem_bytes(P, precision);
   }
   int optin = 0;

@@ -35,7 +35,7 @@ struct AdmmLaunch {
   int warm;
   // launch shape and shared-memory plan (elements of the iteration type)
   int grid, threads;
-  int capB, capI, haloB, haloI, S_max, nv_max;
+  int capB, capI, haloB, haloI, S_max, nv_max, nbuf;
 };
 
 __global__ void set_control_kernel(Ctl *c, int nitems, int batch);
