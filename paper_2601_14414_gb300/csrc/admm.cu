@@ -194,7 +194,7 @@ __device__ __forceinline__ T dot_col(const T *M, int ld, const T *v, int cnt) {
 // The persistent kernel.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
+__global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int sItem, sOk;
@@ -261,11 +261,13 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
       // Copies of the sub-chunk that starts at stage k0 into buffer b (thread 0 issues).
       auto issue = [&](int k0, int b, bool first) {
         const int cnt = min(S, kb - k0);
-        const int ns = cnt + ((k0 + cnt < N) ? 1 : 0);  // plus the next stage
+        const int la = (k0 + cnt < N) ? 1 : 0;  // the next stage: its G and e only
+        const int ns = cnt + la;
         const bool halo = first && ka > 0;
         const uint32_t it_bytes = (uint32_t)(ns * n5p * sizeof(T));
+        const uint32_t blk_bytes = (uint32_t)((cnt * W + la * ((oE + nx + 3) & ~3)) * sizeof(T));
         uint32_t bytes = it_bytes * (use_prev ? 2u : 1u);
-        if (!lti) bytes += (uint32_t)(ns * W * sizeof(T));
+        if (!lti) bytes += blk_bytes;
         if (halo) {
           bytes += (uint32_t)(n5p * sizeof(T)) * (use_prev ? 2u : 1u);
           if (!lti) bytes += (uint32_t)(W * sizeof(T));
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(256) admm_kernel(Args<T> a, Smem lay) {
         mbar_expect_tx(&mbar[b], bytes);
         T *rB = sm + lay.rawB + b * lay.capB;
         T *rI = sm + lay.rawI + b * 2 * lay.capI;
-        if (!lti) bulk_load(rB, blk + (int64_t)k0 * W, (uint32_t)(ns * W * sizeof(T)), &mbar[b]);
+        if (!lti) bulk_load(rB, blk + (int64_t)k0 * W, blk_bytes, &mbar[b]);
         bulk_load(rI, Ic + (int64_t)k0 * n5p, it_bytes, &mbar[b]);
         if (use_prev) bulk_load(rI + lay.capI, Ip + (int64_t)k0 * n5p, it_bytes, &mbar[b]);
         if (halo) {

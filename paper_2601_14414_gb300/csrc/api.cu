@@ -158,7 +158,11 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
     nv_max = std::max(nv_max, tiled ? n : nv);
     W_max = std::max(W_max, w);
     n5p_max = std::max(n5p_max, n5p);
-    if (!lti) capB = std::max<int64_t>(capB, (int64_t)(S + 1) * w);
+    if (!lti) {
+      // S stage blocks plus the next stage's G and e (see the solve kernel's copies)
+      const int ge = tiled ? w : ((nx[j] * odd_ld(n) + nx[j] + 3) & ~3);
+      capB = std::max<int64_t>(capB, (int64_t)S * w + ge);
+    }
     capI = std::max<int64_t>(capI, (int64_t)(S + 1) * n5p);
   }
   // Shared-memory plan of the persistent solve kernel.
