@@ -197,7 +197,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ int sItem, sOk;
+  __shared__ int sItem, sOk, sArr;
   __shared__ double sRed[8];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x;
@@ -303,7 +303,10 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
           if (tid == 0) issue(k0, 0, false);  // the single buffer is free after the last barrier
           pend[0] = true;
         }
-        const bool arrived = mbar_wait(&mbar[b], par[b], ctl);
+        // One thread waits on the copies; the others wait at the barrier without issuing.
+        if (tid == 0) sArr = mbar_wait(&mbar[b], par[b], ctl) ? 1 : 0;
+        __syncthreads();
+        const bool arrived = sArr != 0;
         if (arrived) {
           par[b] ^= 1u;
           pend[b] = false;
