@@ -7,7 +7,7 @@ BATCHED_UNEVEN = dict(
     seed=3,
     batch=4096,
     rho=1.0,
-    eps=1e-9,          # stop test c <= eps (Algorithm 1, step 5)
+    eps=1e-8,          # stop test c <= eps (Algorithm 1, step 5)
     max_iters=4000,
     accel=1,
     eta=0.999,
