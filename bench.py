@@ -43,6 +43,11 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=None, help="instances per GPU (default 4096)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling driver: only the FP32 factorise + solve steps, no reference, "
+                         "e2e or CPU legs; prints the algorithmic bytes of the solve launch")
+    ap.add_argument("--fixed-iters", type=int, default=None,
+                    help="with --profile: run exactly this many iterations (eps < 0)")
     return ap.parse_args()
 
 
@@ -251,6 +256,27 @@ def run_ours(args):
         pimpc.pimpc_set_options(h, cfg["rho"], eps, iters, cfg["accel"], cfg["eta"])
         pimpc.pimpc_set_dynamics(h, d["A"], d["B"], d["e"])
         return h
+
+    if args.profile:
+        eps = -1.0 if args.fixed_iters else cfg["eps"]
+        iters_cap = args.fixed_iters or cfg["max_iters"]
+        h = make(pimpc.F32, eps, iters_cap)
+        u = torch.zeros(tot_u, dtype=torch.float64, device=dev)
+        x = torch.zeros(tot_x, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup + args.steps):
+            pimpc.pimpc_factorise(h, stream.cuda_stream)
+            pimpc.pimpc_solve(h, d["x0"], None, d["ref"], p["ref_per_stage"], 0, u, x)
+        torch.cuda.synchronize()
+        iters = np.zeros(batch, np.int32)
+        mom = np.zeros(batch, np.int32)
+        pimpc.pimpc_get_stats(h, iters, None, None, mom)
+        alg = algorithmic_bytes(nx, nu, N, iters.astype(np.int64), mom.astype(np.int64), 4)
+        if rank == 0:
+            print(json.dumps(dict(profile=True, instances=batch, stages=int(np.sum(N)),
+                                  stage_iterations=int(np.sum(iters * N)),
+                                  algorithmic_bytes_per_solve=alg)), flush=True)
+        pimpc.pimpc_destroy(h)
+        return 0
 
     # FP64 reference solution on this GPU (untimed), scored against in every step.
     href = make(pimpc.F64, cfg["ref_eps"], cfg["ref_max_iters"])
