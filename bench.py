@@ -358,7 +358,7 @@ def run_ours(args):
     solve_s = float(np.mean(solve_ms)) / 1e3
     peak, peak_kind = load_peaks()
     achieved = alg / solve_s / 1e9
-    traffic = profiled_traffic("admm_batched_uneven_ltv_4096.md")
+    traffic = profiled_traffic("admm_kernel_f32_batched_512x30.md")
 
     line = None
     if rank == 0:
