@@ -512,6 +512,7 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
   PIMPC_CHECK(s, s->tiled ? launch_tps(a, s->prec, st) : launch_admm(a, s->prec, st), "solve");
   s->solved = true;
   s->last_ref_per_stage = ref_per_stage;
+  s->last_ref_given = dref != nullptr;
   s->last_warm = warm_start;
   s->last_accel = s->accel;
   s->last_eps = s->eps;

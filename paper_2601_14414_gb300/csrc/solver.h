@@ -36,7 +36,7 @@ struct pimpc_solver {
   double rho = 1.0, eps = 1e-6, eta = 0.999;
   int max_iters = 1000, accel = 1;
   bool stale = true, have_rdu = false, solved = false;
-  int last_ref_per_stage = 0, last_warm = 0, last_accel = 0, last_iters_fixed = 0;
+  int last_ref_per_stage = 0, last_ref_given = 0, last_warm = 0, last_accel = 0, last_iters_fixed = 0;
   double last_eps = 0.0;
   size_t smem_admm = 0;
   int grid_admm = 0;

@@ -318,6 +318,33 @@ class Solver:
         xs = [a.reshape(n, m) for a, n, m in zip(split(x, self.N * self.nx), self.N, self.nx)]
         return dict(u=us, x=xs, iters=it, c=c, status=st)
 
+    def backward(self, dL_du, dL_dx, checkpoint_every=25):
+        """Gradients of L w.r.t. the inputs of the last solve (host memory), given per-instance
+        dL/du [N, nu] and dL/dx [N, nx]; the last solve must have run a fixed number of plain
+        iterations from the zero start (eps < 0, accel = 0, warm_start = 0). Returns per-instance
+        lists x0, q, r, xmin, xmax, umin, umax and ref ([N, n] or [n], like the reference)."""
+        gu = _cat([np.asarray(a, np.float64) for a in dL_du])
+        gx = _cat([np.asarray(a, np.float64) for a in dL_dx])
+        n = self.nx + self.nu
+        per_stage = self.p["ref_per_stage"]
+        out = dict(x0=np.zeros(int(np.sum(self.nx))), q=np.zeros(int(np.sum(self.nx))),
+                   r=np.zeros(int(np.sum(self.nu))), xmin=np.zeros(int(np.sum(self.nx))),
+                   xmax=np.zeros(int(np.sum(self.nx))), umin=np.zeros(int(np.sum(self.nu))),
+                   umax=np.zeros(int(np.sum(self.nu))),
+                   ref=np.zeros(int(np.sum(self.N * n)) if per_stage else int(np.sum(n))))
+        pimpc_backward(self.h, gu, gx, out["x0"], out["ref"], out["q"], out["r"], out["xmin"],
+                       out["xmax"], out["umin"], out["umax"], checkpoint_every)
+        res = {}
+        for key in ("x0", "q", "xmin", "xmax"):
+            res[key] = split(out[key], self.nx)
+        for key in ("r", "umin", "umax"):
+            res[key] = split(out[key], self.nu)
+        if per_stage:
+            res["ref"] = [a.reshape(m, k) for a, m, k in zip(split(out["ref"], self.N * n), self.N, n)]
+        else:
+            res["ref"] = split(out["ref"], n)
+        return res
+
     def iterates(self):
         tot = int(np.sum(self.N * (self.nx + self.nu)))
         arrs = [np.zeros(tot) for _ in range(5)]
