@@ -218,6 +218,45 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
                    double *g_umin, double *g_umax, int checkpoint_every, int mem, void *stream);
 
 /*
+ * Schedules of the batched solve (no counterpart in the paper: how the GPU cuts the work of
+ * Algorithm 1 across its SMs; the arithmetic of an iteration is the same under every schedule,
+ * up to the order of the sums in c).
+ *   family       0: a group of lanes per stage on plain stage blocks (every precision and
+ *                   instance kind; the default); 2: one thread per stage on halo tiles
+ *                   (stage-varying FP32 instances only); -1: the default.
+ *   ctas_per_sm  family 2: CTAs per SM the shared-memory budget of a CTA is sized for
+ *                (0 = 2); ignored by family 0.
+ *   item_scale   family 0: stage sub-chunks per work item (0 = automatic); family 2: at most
+ *                this many tiles per work item (0 = 4).
+ * pimpc_set_schedule re-lays out the stage data and the iterates: the next solve factorises
+ * again and starts cold (warm_start is treated as 0 until one solve has run).
+ * Errors: PIMPC_EINVAL (a bad value, or an instance that does not fit the schedule; the
+ * previous schedule stays in force), PIMPC_ENOMEM, PIMPC_ECUDA.
+ */
+int pimpc_set_schedule(pimpc_solver *s, int family, int ctas_per_sm, int item_scale);
+
+/*
+ * pimpc_get_schedule -- the schedule in force and the launch it gives: grid (CTAs of the
+ * persistent launch), threads (per CTA) and items (work items of one iteration over the whole
+ * batch). Any pointer may be NULL (host memory).
+ */
+int pimpc_get_schedule(pimpc_solver *s, int *family, int *ctas_per_sm, int *item_scale,
+                       int *grid, int *threads, int *items);
+
+/*
+ * pimpc_autotune -- times trial_iters iterations (zero start, no reference, the accel option in
+ * force) of every candidate schedule on this solver's batch, with its current dynamics, weights
+ * and bounds, using CUDA events on `stream`, and keeps the fastest. Candidates: family 0 with
+ * item_scale 0, 2 and 8; family 2 with 1 and 2 CTAs per SM where the batch allows it. The
+ * chosen schedule and its time (ms, the second of two trial solves) are returned through the
+ * pointers (host memory, any may be NULL). The stage cache and the iterates are rebuilt as for
+ * pimpc_set_schedule. Blocks the host until the trials finish.
+ * Errors: PIMPC_EINVAL (trial_iters < 1), PIMPC_ENOMEM, PIMPC_ECUDA.
+ */
+int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_sm,
+                   int *item_scale, double *best_ms, void *stream);
+
+/*
  * pimpc_solve_static -- one instance, solved without allocating any device memory.
  *
  * No counterpart in the paper: this entry point exists for callers that cannot call cudaMalloc

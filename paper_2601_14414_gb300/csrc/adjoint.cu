@@ -26,8 +26,9 @@
 // Work. One CTA per instance (largest instances first), one thread per stage (threads loop when
 // N exceeds the block). All per-stage vectors live in a workspace in global memory, component
 // major ([component][stage]), so that a warp's accesses to one component are coalesced; the
-// stage matrices are read from the solve's stage blocks (G with odd row stride, symmetric H and M
-// as wrapped diagonals). Adjoint arithmetic runs in the iteration precision T; the per-stage
+// stage matrices are read from the solve's stage data in either of its layouts (plain blocks:
+// G with odd row stride, symmetric H and M as wrapped diagonals; halo tiles: element-major
+// slots, H and M packed). Adjoint arithmetic runs in the iteration precision T; the per-stage
 // gradient sums run in FP64. No thread waits on another CTA: only __syncthreads separates phases.
 #include <algorithm>
 #include <vector>
@@ -63,8 +64,9 @@ struct AdjArgs {
 template <typename T>
 struct Inst {
   int nx, nu, n, N, ld, W;
-  const T *blk;          // first stage block
+  const T *blk;          // first stage block (plain) or first tile (halo tiles)
   int lti;
+  int tiled, tw;         // 2: halo tiles of tw slots (W = words per tile), else plain blocks
   int oE, oH, oM;
   const T *qd, *ref, *lo, *hi, *xb0;
   int refstride;         // 0: one reference for all stages
@@ -76,12 +78,26 @@ struct Inst {
   T *xb, *du, *p, *yb, *xbp, *dub;
   double *hsum, *hxsum, *losum, *hisum, *gx0;
 
-  __device__ const T *G(int k) const { return blk + (lti ? 0 : (int64_t)k * W); }
-  __device__ const T *Hb(int k) const {
-    return blk + (lti ? ((k < N - 1) ? 0 : W) : (int64_t)k * W) + oH;
+  // Stage k's block: element e at slot(k)[e * es()].
+  __device__ const T *slot(int k) const {
+    if (tiled == 2) {
+      int t, sl;
+      halo_slot(tw, k, t, sl);
+      return blk + (int64_t)t * W + sl;
+    }
+    return blk + (lti ? 0 : (int64_t)k * W);
   }
-  __device__ const T *Mb(int k) const { return G(k) + oM; }
-  __device__ const T *E(int k) const { return G(k) + oE; }
+  __device__ int es() const { return tiled == 2 ? tw : 1; }
+  // G_k(r, c), e_k(r), H_k(r, c), M_k(r, c) in either layout (plain: G rows of stride ld, H and M
+  // as wrapped diagonals; halo tiles: G row-major, H and M packed lower).
+  __device__ T Gv(int k, int r, int c) const {
+    return tiled == 2 ? slot(k)[(r * n + c) * tw] : slot(k)[r * ld + c];
+  }
+  __device__ T Ev(int k, int r) const {
+    return tiled == 2 ? slot(k)[(nx * n + r) * tw] : slot(k)[oE + r];
+  }
+  __device__ T Hv(int k, int r, int c) const;
+  __device__ T Mv(int k, int r, int c) const;
   __device__ T *st(T *base, int b, int c) const { return base + (int64_t)(b * n + c) * N; }
   __device__ const T *cst(const T *base, int b, int c) const {
     return base + (int64_t)(b * n + c) * N;
@@ -99,6 +115,25 @@ __device__ __forceinline__ T sym_at(const T *Wp, int m, int r, int c) {
 }
 
 template <typename T>
+__device__ T Inst<T>::Hv(int k, int r, int c) const {
+  if (tiled == 2) {
+    const int i = r > c ? r : c, q = r > c ? c : r;
+    return slot(k)[(nx * n + nx + i * (i + 1) / 2 + q) * tw];
+  }
+  const T *b = blk + (lti ? ((k < N - 1) ? 0 : W) : (int64_t)k * W) + oH;
+  return sym_at(b, n, r, c);
+}
+
+template <typename T>
+__device__ T Inst<T>::Mv(int k, int r, int c) const {
+  if (tiled == 2) {
+    const int i = r > c ? r : c, q = r > c ? c : r;
+    return slot(k)[(nx * n + nx + n * (n + 1) / 2 + i * (i + 1) / 2 + q) * tw];
+  }
+  return sym_at(slot(k) + oM, nu, r, c);
+}
+
+template <typename T>
 __device__ void make_inst(const AdjArgs &a, int j, Inst<T> &I) {
   I.nx = a.L.nx[j];
   I.nu = a.L.nu[j];
@@ -107,6 +142,8 @@ __device__ void make_inst(const AdjArgs &a, int j, Inst<T> &I) {
   I.ld = odd_ld(I.n);
   I.W = a.L.W[j];
   I.lti = a.L.lti;
+  I.tiled = a.L.tiled;
+  I.tw = a.L.tiled == 2 ? a.L.tw[j] : 0;
   I.blk = (const T *)a.blk + a.L.blk[j];
   I.oE = I.nx * I.ld;
   I.oH = I.oE + I.nx;
@@ -140,46 +177,41 @@ __device__ void make_inst(const AdjArgs &a, int j, Inst<T> &I) {
 // ---- forward, first half: du_k and xb_k of every stage (Algorithm 1 step 1) ---------------
 template <typename T>
 __device__ void fwd_step1(const Inst<T> &I, const T *S) {
-  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N, ld = I.ld;
+  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N;
   T t[kMaxV], h[kMaxV];
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const T *G = I.G(k);
-    const T *M = I.Mb(k);
     for (int c = 0; c < n; ++c) t[c] = I.cst(S, 1, c)[k] - I.cst(S, 3, c)[k];
     // w = B_k^T t_x + t_u, du = M_k w
     T w[kMaxV];
     for (int q = 0; q < nu; ++q) {
       T s = t[nx + q];
-      for (int r = 0; r < nx; ++r) s += G[r * ld + nx + q] * t[r];
+      for (int r = 0; r < nx; ++r) s += I.Gv(k, r, nx + q) * t[r];
       w[q] = s;
     }
     for (int q = 0; q < nu; ++q) {
       T s = (T)0;
-      for (int i = 0; i < nu; ++i) s += sym_at(M, nu, q, i) * w[i];
+      for (int i = 0; i < nu; ++i) s += I.Mv(k, q, i) * w[i];
       I.du[(int64_t)q * N + k] = s;
     }
     // h = Qbar ref_k + rho (z_k - theta_k + Abar_{k+1}^T y_k)
     for (int c = 0; c < n; ++c) h[c] = (T)0;
     if (k < N - 1) {
-      const T *G1 = I.G(k + 1);
-      const T *e1 = I.E(k + 1);
       T y[kMaxV];
       for (int c = 0; c < n; ++c)
         y[c] = I.cst(S, 0, c)[k + 1] - I.cst(S, 1, c)[k + 1] + I.cst(S, 4, c)[k + 1] -
-               (c < nx ? e1[c] : (T)0);
+               (c < nx ? I.Ev(k + 1, c) : (T)0);
       for (int c = 0; c < n; ++c) {
         T s = c < nx ? (T)0 : y[c];
-        for (int r = 0; r < nx; ++r) s += G1[r * ld + c] * y[r];
+        for (int r = 0; r < nx; ++r) s += I.Gv(k + 1, r, c) * y[r];
         h[c] = s;
       }
     }
     const T *rf = I.refk(k);
     for (int c = 0; c < n; ++c)
       h[c] = I.qd[c] * (rf ? rf[c] : (T)0) + I.rho * (I.cst(S, 0, c)[k] - I.cst(S, 2, c)[k] + h[c]);
-    const T *H = I.Hb(k);
     for (int r = 0; r < n; ++r) {
       T s = (T)0;
-      for (int c = 0; c < n; ++c) s += sym_at(H, n, r, c) * h[c];
+      for (int c = 0; c < n; ++c) s += I.Hv(k, r, c) * h[c];
       I.xb[(int64_t)r * N + k] = s;
     }
   }
@@ -188,19 +220,17 @@ __device__ void fwd_step1(const Inst<T> &I, const T *S) {
 // Abar_k xb_{k-1} (ax), Bbar_k du_k (bd) and ebar_k (ee) of stage k.
 template <typename T>
 __device__ __forceinline__ void stage_products(const Inst<T> &I, int k, T *ax, T *bd, T *ee) {
-  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N, ld = I.ld;
-  const T *G = I.G(k);
-  const T *e = I.E(k);
+  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N;
   T xp[kMaxV];
   for (int c = 0; c < n; ++c) xp[c] = k == 0 ? I.xb0[c] : I.xb[(int64_t)c * N + k - 1];
   for (int r = 0; r < nx; ++r) {
     T s = (T)0;
-    for (int c = 0; c < n; ++c) s += G[r * ld + c] * xp[c];
+    for (int c = 0; c < n; ++c) s += I.Gv(k, r, c) * xp[c];
     ax[r] = s;
     T b = (T)0;
-    for (int q = 0; q < nu; ++q) b += G[r * ld + nx + q] * I.du[(int64_t)q * N + k];
+    for (int q = 0; q < nu; ++q) b += I.Gv(k, r, nx + q) * I.du[(int64_t)q * N + k];
     bd[r] = b;
-    ee[r] = e[r];
+    ee[r] = I.Ev(k, r);
   }
   for (int q = 0; q < nu; ++q) {
     ax[nx + q] = xp[nx + q];
@@ -236,7 +266,7 @@ __device__ void fwd_step23(const Inst<T> &I, const T *S, T *Sout) {
 // ---- reverse of steps 2-3 (and the neighbour term of the previous reverse step 1) ----------
 template <typename T>
 __device__ void rev_step23(const Inst<T> &I, const T *S) {
-  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N, ld = I.ld;
+  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N;
   T ax[kMaxV], bd[kMaxV], ee[kMaxV], axb[kMaxV], bdb[kMaxV];
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     // Adjoint of y_{k-1} = z_k - v_k - ebar_k + lambda_k, left by the later reverse step 1.
@@ -273,17 +303,16 @@ __device__ void rev_step23(const Inst<T> &I, const T *S) {
       I.st(I.sb, 3, c)[k] = beb + gb;
       I.st(I.sb, 4, c)[k] = lab - w23 + gb;
     }
-    const T *G = I.G(k);
     // dubar = Bbar_k^T bdbar
     for (int q = 0; q < nu; ++q) {
       T s = bdb[nx + q];
-      for (int r = 0; r < nx; ++r) s += G[r * ld + nx + q] * bdb[r];
+      for (int r = 0; r < nx; ++r) s += I.Gv(k, r, nx + q) * bdb[r];
       I.dub[(int64_t)q * N + k] = s;
     }
     // Abar_k^T axbar: to xb_{k-1} (read by the thread of stage k-1), or to xbar_0 = (x0, u_prev).
     for (int c = 0; c < n; ++c) {
       T s = c < nx ? (T)0 : axb[c];
-      for (int r = 0; r < nx; ++r) s += G[r * ld + c] * axb[r];
+      for (int r = 0; r < nx; ++r) s += I.Gv(k, r, c) * axb[r];
       if (k > 0) I.p[(int64_t)c * N + k] = s;
       else if (c < nx) I.gx0[c] += (double)s;
     }
@@ -293,15 +322,14 @@ __device__ void rev_step23(const Inst<T> &I, const T *S) {
 // ---- reverse of step 1 -----------------------------------------------------------------------
 template <typename T>
 __device__ void rev_step1(const Inst<T> &I) {
-  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N, ld = I.ld;
+  const int nx = I.nx, nu = I.nu, n = I.n, N = I.N;
   T xt[kMaxV], hb[kMaxV], m[kMaxV];
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     for (int c = 0; c < n; ++c)
       xt[c] = I.xbp[(int64_t)c * N + k] + (k < N - 1 ? I.p[(int64_t)c * N + k + 1] : (T)0);
-    const T *H = I.Hb(k);
     for (int r = 0; r < n; ++r) {
       T s = (T)0;
-      for (int c = 0; c < n; ++c) s += sym_at(H, n, r, c) * xt[c];
+      for (int c = 0; c < n; ++c) s += I.Hv(k, r, c) * xt[c];
       hb[r] = s;
     }
     for (int c = 0; c < n; ++c) {
@@ -312,25 +340,22 @@ __device__ void rev_step1(const Inst<T> &I) {
     }
     if (k < N - 1) {
       // ybar = Abar_{k+1} (rho hbar): [A x_x + B x_u ; x_u]
-      const T *G1 = I.G(k + 1);
       for (int r = 0; r < nx; ++r) {
         T s = (T)0;
-        for (int c = 0; c < n; ++c) s += G1[r * ld + c] * (I.rho * hb[c]);
+        for (int c = 0; c < n; ++c) s += I.Gv(k + 1, r, c) * (I.rho * hb[c]);
         I.yb[(int64_t)r * N + k] = s;
       }
       for (int q = 0; q < nu; ++q) I.yb[(int64_t)(nx + q) * N + k] = I.rho * hb[nx + q];
     }
     // tbar = Bbar_k M_k dubar -> v_k (+), beta_k (-)
-    const T *M = I.Mb(k);
     for (int q = 0; q < nu; ++q) {
       T s = (T)0;
-      for (int i = 0; i < nu; ++i) s += sym_at(M, nu, q, i) * I.dub[(int64_t)i * N + k];
+      for (int i = 0; i < nu; ++i) s += I.Mv(k, q, i) * I.dub[(int64_t)i * N + k];
       m[q] = s;
     }
-    const T *G = I.G(k);
     for (int r = 0; r < nx; ++r) {
       T s = (T)0;
-      for (int q = 0; q < nu; ++q) s += G[r * ld + nx + q] * m[q];
+      for (int q = 0; q < nu; ++q) s += I.Gv(k, r, nx + q) * m[q];
       I.st(I.sb, 1, r)[k] += s;
       I.st(I.sb, 3, r)[k] -= s;
     }
@@ -456,7 +481,7 @@ extern "C" int pimpc_backward(pimpc_solver *s, const double *dL_du, const double
   if (s->last_warm != 0 || s->last_accel != 0 || s->last_eps >= 0.0)
     return fail(s, PIMPC_ESTATE,
                 "the last solve must use warm_start = 0, accel = 0 and eps < 0 (fixed iterations)");
-  if (s->tiled) return fail(s, PIMPC_ESTATE, "the adjoint reads the plain stage layout");
+  if (s->tiled == 1) return fail(s, PIMPC_ESTATE, "the adjoint does not read the 32-stage tiled layout");
   cudaStream_t st = (cudaStream_t)stream;
   cudaSetDevice(s->device);
   const int Tn = s->last_iters_fixed;

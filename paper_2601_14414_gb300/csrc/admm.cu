@@ -1,5 +1,6 @@
-// admm.cu -- Algorithm 1 with a group of lanes per stage, used for stage-invariant instances
-// with 32 < n <= 64 (smaller instances use the one-thread-per-stage kernel of admm_tps.cu).
+// admm.cu -- Algorithm 1 with a group of lanes per stage on plain stage blocks: stage-invariant
+// instances (n <= 64) and every FP64 solve. (Stage-varying FP32 instances run one thread per
+// stage on halo tiles, admm_tile.cu.)
 //
 // Work decomposition. The stages of every instance are cut into items of consecutive stages
 // (item = instance j, stages [a, b)). One cooperative launch runs all iterations of all
@@ -16,9 +17,11 @@
 //
 // Data movement. Stage blocks (G_k = [A_k | B_k] row-major, e_k, H_k and M_k stored diagonal by
 // diagonal) and the iterates of a sub-chunk of S stages (plus the next stage) arrive in shared
-// memory by cp.async.bulk copies completing on an mbarrier, double-buffered: the copies of
-// sub-chunk s+1 are in flight while sub-chunk s is computed. Every wait is bounded; a timeout
-// raises an error flag that ends the launch (no instance is marked converged).
+// memory by cp.async.bulk copies completing on an mbarrier; with one buffer (the default) the
+// copies of the next sub-chunk are issued after the current one is computed and the other CTAs
+// resident on the SM hide the latency, with two buffers they overlap the compute. Every wait is
+// bounded; a timeout raises an error flag that ends the launch (no instance is marked
+// converged).
 //
 // Iterates. Three buffers rotate: iteration i reads cur = buf[(base + i) % 3] and, when the
 // momentum factor f_i = (alpha_i - 1) / alpha_{i+1} is nonzero, prev = buf[(base + i - 1) % 3];
@@ -36,6 +39,7 @@
 
 #include <algorithm>
 
+#include "bulk.cuh"
 #include "lockstep.cuh"
 
 namespace pimpc {
@@ -49,43 +53,7 @@ __global__ void set_control_kernel(Ctl *c, int nitems, int batch) {
 namespace {
 
 using ls::kWaitLimit;
-
-// ---------------------------------------------------------------------------------------------
-// PTX helpers: mbarrier + bulk asynchronous copies (the non-tensor TMA form).
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Orders this thread's earlier generic-proxy accesses (and those it has observed) before later
-// async-proxy (bulk copy) accesses, for both shared and global memory.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
+using namespace bulk;
 
 template <typename T>
 using Args = ls::Args<T>;
@@ -126,17 +94,6 @@ __device__ inline T clampv(T x, T lo, T hi) {
   return x < lo ? lo : (x > hi ? hi : x);
 }
 
-// Bounded wait on an mbarrier phase (every thread polls); false and an error flag on timeout.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, Ctl *c) {
-  long long k = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if (++k > kWaitLimit) {
-      atomicExch(&c->err, 2);
-      return false;
-    }
-  }
-  return true;
-}
 
 // (S x)_c for a symmetric m x m matrix S stored as wrapped diagonals: row d (d <= m/2) holds
 // S[c][(c + d) mod m]; S[c][(c - d) mod m] = S[(c - d) mod m][c] is entry (c - d) mod m of row d.

@@ -73,6 +73,252 @@ bool finite_or_inf_ok(const double *p, int64_t n) {
 
 }  // namespace
 
+
+namespace {
+
+void free_layout(pimpc_solver *s) {
+  for (void *p : s->lay_allocs) cudaFree(p);
+  s->lay_allocs.clear();
+  s->blk_T = nullptr;
+  for (int b = 0; b < 3; ++b) s->it[b] = nullptr;
+  s->item_inst = s->item_a = s->item_b = s->list0 = s->list1 = nullptr;
+}
+
+template <typename P>
+cudaError_t lalloc(pimpc_solver *s, P **p, size_t bytes) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  s->lay_allocs.push_back(q);
+  *p = (P *)q;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+namespace pimpc {
+
+// Lays out the stage blocks and iterates for a schedule, plans the solve kernel's launch and
+// work items, and (re)allocates the buffers that depend on them. The iterates restart from zero
+// and the factorisation is redone at the next solve.
+int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
+  Schedule sc = sc_in;
+  const int batch = s->batch, lti = s->lti, precision = s->prec;
+  const size_t ts = tsize(precision);
+  const std::vector<int> &nx = s->nx, &nu = s->nu, &N = s->N;
+  if (sc.family < 0) sc.family = 0;  // lane groups; halo tiles are chosen explicitly or by the autotuner
+  if (sc.family != 0 && sc.family != 2) { why = "schedule family must be 0 or 2"; return PIMPC_EINVAL; }
+  if (sc.family == 2 && (precision != PIMPC_F32 || lti)) {
+    why = "halo tiles serve stage-varying FP32 instances";
+    return PIMPC_EINVAL;
+  }
+  if (sc.ctas_per_sm < 0 || sc.ctas_per_sm > 8 || sc.item_scale < 0 || sc.item_scale > 64) {
+    why = "schedule: ctas_per_sm in 0..8, item_scale in 0..64";
+    return PIMPC_EINVAL;
+  }
+  const int tiled = sc.family;
+  s->tiled = tiled;
+  int nsm = 0, smem_sm = 0, optin = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+  std::vector<int> W(batch), tw(batch, 0);
+  std::vector<int64_t> blk(batch), Ni(batch);
+  int64_t tot_blk = 0, tot_Ni = 0;
+  AdmmLaunch P{};
+  std::vector<int> item_inst, item_a, item_b, nitems_inst(batch, 0);
+  // Instance order: largest streamed volume first.
+  std::vector<int> order(batch);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> cost(batch);
+  for (int j = 0; j < batch; ++j) {
+    const int n = nx[j] + nu[j];
+    cost[j] = (double)N[j] * ((lti ? 0.0 : (double)packed_block_words(nx[j], nu[j])) + 15.0 * n);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  int bps = 0;
+  cudaError_t e = cudaSuccess;
+  if (tiled == 2) {
+    // Shared-memory budget of one CTA, and per instance the widest tile that fits it.
+    const int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 2;
+    int64_t D = (int64_t)smem_sm / cps - 1024 - 256;
+    D = std::min<int64_t>(D, optin - 256);
+    D = D / 128 * 128;
+    const int max_tiles = sc.item_scale > 0 ? std::min(sc.item_scale, tile_warps()) : tile_warps();
+    auto tile_bytes = [&](int j, int w) {
+      const int n = nx[j] + nu[j];
+      return (int64_t)(tile_block_words(w, nx[j], nu[j]) + 2 * tile_iter_words(w, n) + 4 * n * w) *
+             (int64_t)ts;
+    };
+    for (int j = 0; j < batch; ++j) {
+      const int n = nx[j] + nu[j];
+      int w = 0;
+      for (int cand : {32, 16})
+        if (tile_bytes(j, cand) <= D) { w = cand; break; }
+      if (w == 0) {
+        char b[200];
+        snprintf(b, sizeof b, "instance %d (nx %d, nu %d) does not fit a halo tile in %lld bytes",
+                 j, nx[j], nu[j], (long long)D);
+        why = b;
+        return PIMPC_EINVAL;
+      }
+      tw[j] = w;
+      const int nt = halo_tiles(N[j], w);
+      W[j] = tile_block_words(w, nx[j], nu[j]);
+      blk[j] = tot_blk;
+      tot_blk += ((int64_t)nt * W[j] + 31) / 32 * 32;
+      Ni[j] = tot_Ni;
+      tot_Ni += ((int64_t)nt * tile_iter_words(w, n) + 31) / 32 * 32;
+    }
+    for (int oi = 0; oi < batch; ++oi) {
+      const int j = order[oi];
+      const int nt = halo_tiles(N[j], tw[j]);
+      const int m = (int)std::max<int64_t>(1, std::min<int64_t>(max_tiles, D / tile_bytes(j, tw[j])));
+      for (int t0 = 0; t0 < nt; t0 += m) {
+        item_inst.push_back(j);
+        item_a.push_back(t0);
+        item_b.push_back(std::min(nt, t0 + m));
+        nitems_inst[j] += 1;
+      }
+    }
+    P.threads = tile_threads();
+    P.capB = (int)(D / (int64_t)ts);
+    s->smem_admm = (size_t)D;
+    e = tile_configure(s->smem_admm, &bps);
+  } else {
+    const int threads = admm_threads(precision);
+    int nv_max = 2, W_max = 4, n5p_max = 4, scr_max = 4, xrows_max = 4;
+    int64_t capB = 0, capI = 0, total_sub = 0;
+    for (int j = 0; j < batch; ++j) {
+      const int n = nx[j] + nu[j];
+      const int n5p = admm_iter_stride(n, precision);
+      W[j] = block_words(nx[j], nu[j]);
+      blk[j] = tot_blk;
+      tot_blk += ((int64_t)blocks_per_instance(lti, N[j]) * W[j] + 31) / 32 * 32;
+      Ni[j] = tot_Ni;
+      tot_Ni += ((int64_t)N[j] * n5p + 31) / 32 * 32;
+      const int S = threads / admm_group_size(n);
+      const int nv = (n + 3) & ~3;
+      scr_max = std::max(scr_max, S * 4 * nv);            // per-group scratch rows
+      xrows_max = std::max(xrows_max, 2 * (S + 1) * nv);  // double-buffered xbar rows
+      nv_max = std::max(nv_max, nv);
+      W_max = std::max(W_max, W[j]);
+      n5p_max = std::max(n5p_max, n5p);
+      if (!lti) {
+        // S stage blocks plus the next stage's G and e (see the solve kernel's copies)
+        const int ge = (nx[j] * odd_ld(n) + nx[j] + 3) & ~3;
+        capB = std::max<int64_t>(capB, (int64_t)S * W[j] + ge);
+      }
+      capI = std::max<int64_t>(capI, (int64_t)(S + 1) * n5p);
+      total_sub += (N[j] + S - 1) / S;
+    }
+    P.threads = threads;
+    P.capB = (int)capB;
+    P.capI = (int)capI;
+    P.haloB = lti ? 2 * W_max : W_max;
+    P.haloI = 2 * n5p_max;
+    P.S_max = scr_max;    // the lane-group kernel's plan takes the scratch and xbar-row sizes
+    P.nv_max = xrows_max;
+    P.nbuf = 1;
+    s->smem_admm = admm_smem_bytes(P, precision);
+    if (s->smem_admm + 1024 > (size_t)optin) {
+      why = "an instance needs more shared memory than one CTA has at this precision";
+      return PIMPC_EINVAL;
+    }
+    e = admm_configure(precision, s->smem_admm, &bps);
+    if (e == cudaSuccess && bps >= 1) {
+      const int64_t max_grid = (int64_t)bps * nsm;
+      // Sub-chunks per item: enough items for about 4 per CTA, at most 16 sub-chunks per item.
+      int64_t m = sc.item_scale > 0 ? sc.item_scale : total_sub / (4 * max_grid);
+      m = std::max<int64_t>(1, std::min<int64_t>(sc.item_scale > 0 ? 64 : 16, m));
+      for (int oi = 0; oi < batch; ++oi) {
+        const int j = order[oi];
+        const int n = nx[j] + nu[j];
+        const int S = threads / admm_group_size(n);
+        int is = (int)(S * m);
+        if (lti) is = std::max(is, std::min(N[j], (256 + S - 1) / S * S));
+        for (int a0 = 0; a0 < N[j]; a0 += is) {
+          item_inst.push_back(j);
+          item_a.push_back(a0);
+          item_b.push_back(std::min(N[j], a0 + is));
+          nitems_inst[j] += 1;
+        }
+      }
+    }
+  }
+  if (e != cudaSuccess || bps < 1) {
+    why = std::string("kernel configuration failed: ") +
+          (e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy");
+    return PIMPC_ECUDA;
+  }
+  const int nitems = (int)item_inst.size();
+  const int grid = (int)std::min<int64_t>((int64_t)bps * nsm, nitems);
+
+  // (Re)allocate and upload what depends on the schedule.
+  cudaDeviceSynchronize();
+  free_layout(s);
+  e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  int64_t *d_blk = nullptr, *d_Ni = nullptr;
+  int *d_W = nullptr, *d_tw = nullptr;
+  chk(lalloc(s, &s->blk_T, ts * tot_blk));
+  for (int b = 0; b < 3; ++b) chk(lalloc(s, &s->it[b], ts * tot_Ni));
+  chk(lalloc(s, &s->item_inst, sizeof(int) * nitems));
+  chk(lalloc(s, &s->item_a, sizeof(int) * nitems));
+  chk(lalloc(s, &s->item_b, sizeof(int) * nitems));
+  chk(lalloc(s, &s->list0, sizeof(int) * nitems));
+  chk(lalloc(s, &s->list1, sizeof(int) * nitems));
+  chk(lalloc(s, &d_blk, sizeof(int64_t) * batch));
+  chk(lalloc(s, &d_Ni, sizeof(int64_t) * batch));
+  chk(lalloc(s, &d_W, sizeof(int) * batch));
+  chk(lalloc(s, &d_tw, sizeof(int) * batch));
+  if (e != cudaSuccess) {
+    why = std::string("device allocation failed: ") + cudaGetErrorString(e);
+    const bool oom = e == cudaErrorMemoryAllocation;
+    free_layout(s);
+    (void)cudaGetLastError();
+    return oom ? PIMPC_ENOMEM : PIMPC_ECUDA;
+  }
+  chk(cudaMemcpy(s->item_inst, item_inst.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_a, item_a.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_b, item_b.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->nitems_inst, nitems_inst.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(d_blk, blk.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(d_Ni, Ni.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(d_W, W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(d_tw, tw.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemset(s->blk_T, 0, ts * tot_blk));
+  for (int b = 0; b < 3; ++b) chk(cudaMemset(s->it[b], 0, ts * tot_Ni));
+  chk(cudaMemset(s->base, 0, sizeof(int) * batch));
+  chk(cudaDeviceSynchronize());
+  if (e != cudaSuccess) {
+    why = std::string("device initialisation failed: ") + cudaGetErrorString(e);
+    free_layout(s);
+    return PIMPC_ECUDA;
+  }
+  s->W = W;
+  s->tw = tw;
+  s->blk = blk;
+  s->Ni = Ni;
+  s->tot_blk = tot_blk;
+  s->tot_Ni = tot_Ni;
+  s->nitems = nitems;
+  s->grid_admm = grid;
+  P.grid = grid;
+  s->plan = P;
+  s->sched = sc;
+  s->L.tiled = tiled;
+  s->L.tw = tiled == 2 ? d_tw : nullptr;
+  s->L.blk = d_blk;
+  s->L.Ni = d_Ni;
+  s->L.W = d_W;
+  s->stale = true;
+  s->solved = false;
+  return PIMPC_OK;
+}
+
+}  // namespace pimpc
+
 extern "C" {
 
 const char *pimpc_last_error(const pimpc_solver *s) {
@@ -84,6 +330,7 @@ void pimpc_destroy(pimpc_solver *s) {
   cudaSetDevice(s->device);
   cudaDeviceSynchronize();
   for (void *p : s->allocs) cudaFree(p);
+  for (void *p : s->lay_allocs) cudaFree(p);
   if (s->adj_ws) cudaFree(s->adj_ws);
   if (s->mask_alloc) cudaFree(s->mask_alloc);
   delete s;
@@ -116,122 +363,26 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   s->device = device; s->batch = batch; s->lti = lti; s->prec = precision;
   s->nx.assign(nx, nx + batch); s->nu.assign(nu, nu + batch); s->N.assign(N, N + batch);
   auto grow = [&](std::vector<int64_t> &v, int64_t &tot, int64_t add) { v.push_back(tot); tot += add; };
-  // The batched solve runs the lane-group kernel on plain stage blocks. (The one-thread-per-stage
-  // kernel on the 32-stage tiled layout serves pimpc_solve_static.)
-  const int tiled = 0;
-  s->tiled = tiled;
-  const int threads = tiled ? tps_threads() : admm_threads(precision);
   const size_t ts = tsize(precision);
-  int S_max = 1, nv_max = 2, W_max = 4, n5p_max = 4, scr_max = 4, xrows_max = 4;
-  int64_t capB = 0, capI = 0;
   int64_t stage_acc = 0;
   for (int j = 0; j < batch; ++j) {
     const int n = nx[j] + nu[j];
-    const int n5p = admm_iter_stride(n, precision);
-    const int64_t ntiles = (N[j] + 31) / 32;
     grow(s->off_nx, s->tot_nx, nx[j]);
     grow(s->off_nu, s->tot_nu, nu[j]);
     grow(s->off_n, s->tot_n, n);
     grow(s->Nnx, s->tot_Nnx, (int64_t)N[j] * nx[j]);
     grow(s->Nnu, s->tot_Nnu, (int64_t)N[j] * nu[j]);
     grow(s->Nn, s->tot_Nn, (int64_t)N[j] * n);
-    grow(s->Ni, s->tot_Ni, tiled ? ntiles * 32 * 5 * n : (int64_t)N[j] * n5p);
     const int64_t reps = lti ? 1 : N[j];
     grow(s->offA, s->tot_A, reps * nx[j] * nx[j]);
     grow(s->offB, s->tot_B, reps * nx[j] * nu[j]);
     grow(s->offe, s->tot_e, reps * nx[j]);
-    const int w = tiled ? nx[j] * n + nx[j] + n * (n + 1) / 2 + nu[j] * (nu[j] + 1) / 2
-                        : block_words(nx[j], nu[j]);
-    s->W.push_back(w);
-    const int64_t blk_words = (tiled && !lti) ? ntiles * 32 * w : (int64_t)blocks_per_instance(lti, N[j]) * w;
-    grow(s->blk, s->tot_blk, (blk_words + 31) / 32 * 32);
     s->stage0.push_back(stage_acc);
     stage_acc += N[j];
     grow(s->bbase, s->nblocks, blocks_per_instance(lti, N[j]));
     s->max_nx = std::max(s->max_nx, nx[j]);
     s->max_n = std::max(s->max_n, n);
-    const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
-    const int nv = (n + 3) & ~3;
-    scr_max = std::max(scr_max, S * 4 * nv);        // per-group scratch rows
-    xrows_max = std::max(xrows_max, 2 * (S + 1) * nv);  // double-buffered xbar rows
-    S_max = std::max(S_max, S);
-    nv_max = std::max(nv_max, tiled ? n : nv);
-    W_max = std::max(W_max, w);
-    n5p_max = std::max(n5p_max, n5p);
-    if (!lti) {
-      // S stage blocks plus the next stage's G and e (see the solve kernel's copies)
-      const int ge = tiled ? w : ((nx[j] * odd_ld(n) + nx[j] + 3) & ~3);
-      capB = std::max<int64_t>(capB, (int64_t)S * w + ge);
-    }
-    capI = std::max<int64_t>(capI, (int64_t)(S + 1) * n5p);
   }
-  // Shared-memory plan of the persistent solve kernel.
-  AdmmLaunch &P = s->plan;
-  P.threads = threads;
-  if (tiled) {
-    P.nv_max = s->max_n;
-    s->smem_admm = tps_smem_bytes(s->max_n, precision);
-  } else {
-    P.capB = (int)capB;
-    P.capI = (int)capI;
-    P.haloB = lti ? 2 * W_max : W_max;
-    P.haloI = 2 * n5p_max;
-    P.S_max = scr_max;    // the lane-group kernel's plan takes the scratch and xbar-row sizes
-    P.nv_max = xrows_max;
-    P.nbuf = 1;
-    s->smem_admm = admm_smem_bytes(P, precision);
-  }
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  if (s->smem_admm + 1024 > (size_t)optin) {
-    g_create_error = "an instance needs more shared memory than one CTA has at this precision";
-    delete s;
-    return PIMPC_EINVAL;
-  }
-  // Instance order (largest streamed volume first) and its work items.
-  std::vector<int> order(batch);
-  std::iota(order.begin(), order.end(), 0);
-  std::vector<double> cost(batch);
-  int64_t total_sub = 0;
-  for (int j = 0; j < batch; ++j) {
-    const int n = nx[j] + nu[j];
-    cost[j] = (double)N[j] * ((lti ? 0 : s->W[j]) + 15.0 * n);
-    const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
-    total_sub += (N[j] + S - 1) / S;
-  }
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  int bps = 0, nsm = 0;
-  cudaError_t e = tiled ? tps_configure(precision, s->smem_admm, &bps)
-                        : admm_configure(precision, s->smem_admm, &bps);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-  if (e != cudaSuccess || bps < 1) {
-    g_create_error = std::string("kernel configuration failed: ") +
-                     (e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy");
-    delete s;
-    return PIMPC_ECUDA;
-  }
-  const int64_t max_grid = (int64_t)bps * nsm;
-  // Sub-chunks per item: enough items for about 4 per CTA, at most 16 sub-chunks per item.
-  int64_t m = total_sub / (4 * max_grid);
-  m = std::max<int64_t>(1, std::min<int64_t>(16, m));
-  std::vector<int> item_inst, item_a, item_b, nitems_inst(batch, 0);
-  for (int oi = 0; oi < batch; ++oi) {
-    const int j = order[oi];
-    const int n = nx[j] + nu[j];
-    const int S = tiled ? tps_stages_per_subchunk() : threads / admm_group_size(n);
-    int is = (int)(S * m);
-    if (lti && !tiled) is = std::max(is, std::min(N[j], (256 + S - 1) / S * S));
-    for (int a0 = 0; a0 < N[j]; a0 += is) {
-      item_inst.push_back(j);
-      item_a.push_back(a0);
-      item_b.push_back(std::min(N[j], a0 + is));
-      nitems_inst[j] += 1;
-    }
-  }
-  s->nitems = (int)item_inst.size();
-  s->grid_admm = (int)std::min<int64_t>(max_grid, s->nitems);
-  P.grid = s->grid_admm;
-
   std::vector<int> binst(s->nblocks);
   for (int j = 0; j < batch; ++j)
     for (int b = 0; b < blocks_per_instance(lti, N[j]); ++b) binst[s->bbase[j] + b] = j;
@@ -241,26 +392,25 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
        s->tot_Nnx + s->tot_Nnu + 8 * (int64_t)batch, s->tot_Nnx + s->tot_Nnu + 2 * s->tot_Nn,
        s->tot_n + s->tot_Nn});
   s->stage_words = stage_words;
-  e = cudaSuccess;
+  cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  std::vector<int64_t> *h_off[13] = {&s->off_nx, &s->off_nu, &s->off_n, &s->Nnx, &s->Nnu, &s->Nn,
-                                     &s->offA, &s->offB, &s->offe, &s->blk, &s->stage0, &s->bbase,
-                                     &s->Ni};
-  int64_t *d_off[13];
-  for (int i = 0; i < 13; ++i) {
+  std::vector<int64_t> *h_off[10] = {&s->off_nx, &s->off_nu, &s->off_n, &s->Nnx, &s->Nnu, &s->Nn,
+                                     &s->offA, &s->offB, &s->offe, &s->stage0};
+  int64_t *d_off[10];
+  for (int i = 0; i < 10; ++i) {
     chk(dalloc(s, &d_off[i], sizeof(int64_t) * batch));
     if (e == cudaSuccess) chk(cudaMemcpy(d_off[i], h_off[i]->data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   }
-  int *d_nx = nullptr, *d_nu = nullptr, *d_N = nullptr, *d_W = nullptr;
+  int *d_nx = nullptr, *d_nu = nullptr, *d_N = nullptr;
   chk(dalloc(s, &d_nx, sizeof(int) * batch));
   chk(dalloc(s, &d_nu, sizeof(int) * batch));
   chk(dalloc(s, &d_N, sizeof(int) * batch));
-  chk(dalloc(s, &d_W, sizeof(int) * batch));
+  chk(dalloc(s, &s->d_bbase, sizeof(int64_t) * batch));
   if (e == cudaSuccess) {
     chk(cudaMemcpy(d_nx, nx, sizeof(int) * batch, cudaMemcpyHostToDevice));
     chk(cudaMemcpy(d_nu, nu, sizeof(int) * batch, cudaMemcpyHostToDevice));
     chk(cudaMemcpy(d_N, N, sizeof(int) * batch, cudaMemcpyHostToDevice));
-    chk(cudaMemcpy(d_W, s->W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(s->d_bbase, s->bbase.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   }
   chk(dalloc(s, &s->A64, sizeof(double) * s->tot_A));
   chk(dalloc(s, &s->B64, sizeof(double) * s->tot_B));
@@ -270,8 +420,6 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(dalloc(s, &s->stage64, sizeof(double) * stage_words));
   chk(dalloc(s, &s->out_u, sizeof(double) * s->tot_Nnu));
   chk(dalloc(s, &s->out_x, sizeof(double) * s->tot_Nnx));
-  chk(dalloc(s, &s->blk_T, ts * s->tot_blk));
-  for (int b = 0; b < 3; ++b) chk(dalloc(s, &s->it[b], ts * s->tot_Ni));
   chk(dalloc(s, &s->qd_T, ts * s->tot_n));
   chk(dalloc(s, &s->ref_T, ts * std::max(s->tot_Nn, s->tot_n)));
   chk(dalloc(s, &s->lo_T, ts * s->tot_n));
@@ -285,12 +433,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(dalloc(s, &s->cacc, sizeof(double) * batch));
   chk(dalloc(s, &s->ndone, sizeof(int) * batch));
   chk(dalloc(s, &s->stop, sizeof(int) * batch));
-  chk(dalloc(s, &s->item_inst, sizeof(int) * s->nitems));
-  chk(dalloc(s, &s->item_a, sizeof(int) * s->nitems));
-  chk(dalloc(s, &s->item_b, sizeof(int) * s->nitems));
   chk(dalloc(s, &s->nitems_inst, sizeof(int) * batch));
-  chk(dalloc(s, &s->list0, sizeof(int) * s->nitems));
-  chk(dalloc(s, &s->list1, sizeof(int) * s->nitems));
   chk(dalloc(s, &s->ctl, sizeof(Ctl)));
   chk(dalloc(s, &s->binst, sizeof(int) * s->nblocks));
   chk(dalloc(s, &s->ferr, sizeof(int) * 4));
@@ -301,11 +444,6 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
     pimpc_destroy(s);
     return oom ? PIMPC_ENOMEM : PIMPC_ECUDA;
   }
-  s->d_bbase = d_off[11];
-  chk(cudaMemcpy(s->item_inst, item_inst.data(), sizeof(int) * s->nitems, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(s->item_a, item_a.data(), sizeof(int) * s->nitems, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(s->item_b, item_b.data(), sizeof(int) * s->nitems, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(s->nitems_inst, nitems_inst.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(s->binst, binst.data(), sizeof(int) * s->nblocks, cudaMemcpyHostToDevice));
   chk(cudaMemset(s->A64, 0, sizeof(double) * s->tot_A));
   chk(cudaMemset(s->B64, 0, sizeof(double) * s->tot_B));
@@ -313,9 +451,6 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(cudaMemset(s->qd64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->rdu64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->qd_T, 0, ts * s->tot_n));
-  chk(cudaMemset(s->blk_T, 0, ts * s->tot_blk));
-  for (int b = 0; b < 3; ++b) chk(cudaMemset(s->it[b], 0, ts * s->tot_Ni));
-  chk(cudaMemset(s->base, 0, sizeof(int) * batch));
   chk(cudaMemset(s->ferr, 0, sizeof(int) * 4));
   chk(cudaMemset(s->st, 0, sizeof(InstState) * batch));
   {
@@ -337,8 +472,14 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   L.off_nx = d_off[0]; L.off_nu = d_off[1]; L.off_n = d_off[2];
   L.Nnx = d_off[3]; L.Nnu = d_off[4]; L.Nn = d_off[5];
   L.offA = d_off[6]; L.offB = d_off[7]; L.offe = d_off[8];
-  L.blk = d_off[9]; L.W = d_W; L.stage0 = d_off[10]; L.Ni = d_off[12];
-  L.tiled = tiled;
+  L.stage0 = d_off[9];
+  std::string why;
+  const int rc = apply_schedule(s, Schedule{}, why);
+  if (rc != PIMPC_OK) {
+    g_create_error = why;
+    pimpc_destroy(s);
+    return rc;
+  }
   *out = s;
   return PIMPC_OK;
 }
@@ -509,7 +650,7 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
   const bool dev = mem == PIMPC_DEVICE;
   a.u_out = u_out ? (dev ? u_out : s->out_u) : nullptr;
   a.x_out = x_out ? (dev ? x_out : s->out_x) : nullptr;
-  PIMPC_CHECK(s, s->tiled ? launch_tps(a, s->prec, st) : launch_admm(a, s->prec, st), "solve");
+  PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st) : launch_admm(a, s->prec, st), "solve");
   s->solved = true;
   s->last_ref_per_stage = ref_per_stage;
   s->last_ref_given = dref != nullptr;

@@ -122,17 +122,29 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   const int oE = nx * ldg, oH = oE + nx;
   const int oM = oH + (tiled ? packed_size(n) : wrapped_size(n));
   // Element e of this block: tiled stage-varying data interleaves 32 stages element-major;
-  // everything else is a plain block.
-  T *base;
-  int es;
-  if (tiled && !lti) {
-    base = blk + a.L.blk[j] + (int64_t)(kb >> 5) * 32 * W + (kb & 31);
+  // halo tiles interleave tw slots and hold the stage up to three times (its own slot and the
+  // halo slots of the neighbouring tiles); everything else is a plain block.
+  T *bases[3];
+  int nb = 1, es;
+  if (a.L.tiled == 2) {
+    const int tw = a.L.tw[j];
+    int t, sl, tt[2], ss[2];
+    halo_slot(tw, kb, t, sl);
+    es = tw;
+    bases[0] = blk + a.L.blk[j] + (int64_t)t * W + sl;
+    const int m = halo_copies(tw, N, kb, tt, ss);
+    for (int q = 0; q < m; ++q) bases[1 + q] = blk + a.L.blk[j] + (int64_t)tt[q] * W + ss[q];
+    nb = 1 + m;
+  } else if (tiled && !lti) {
+    bases[0] = blk + a.L.blk[j] + (int64_t)(kb >> 5) * 32 * W + (kb & 31);
     es = 32;
   } else {
-    base = blk + a.L.blk[j] + (int64_t)kb * W;
+    bases[0] = blk + a.L.blk[j] + (int64_t)kb * W;
     es = 1;
   }
-  auto put = [&](int e, double v) { base[(int64_t)e * es] = (T)v; };
+  auto put = [&](int e, double v) {
+    for (int q = 0; q < nb; ++q) bases[q][(int64_t)e * es] = (T)v;
+  };
   // Symmetric matrices: packed lower row-major (one-thread-per-stage kernel) or wrapped
   // diagonals, row d holding S[c][(c + d) mod m] (lane-group kernel).
   auto put_sym = [&](int o, int m, const double *Xs, int ldx) {
@@ -170,8 +182,10 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     }
   chol_inverse(S, X, nu, nu, lane, a.err);
   put_sym(oM, nu, X, nu);
-  const int end = oM + (tiled ? packed_size(nu) : wrapped_size(nu));
-  for (int w = end + lane; w < W; w += 32) put(w, 0.0);
+  if (!tiled) {  // padding of a plain block
+    const int end = oM + wrapped_size(nu);
+    for (int w = end + lane; w < W; w += 32) put(w, 0.0);
+  }
 }
 
 }  // namespace

@@ -46,6 +46,21 @@ size_t admm_smem_bytes(const AdmmLaunch &s, int precision);
 cudaError_t admm_configure(int precision, size_t smem, int *blocks_per_sm);
 cudaError_t launch_admm(const AdmmLaunch &a, int precision, cudaStream_t stream);
 
+// One thread per stage on halo tiles (stage-varying FP32 instances).
+int tile_threads();
+int tile_warps();
+cudaError_t tile_configure(size_t smem, int *blocks_per_sm);
+cudaError_t launch_tile(const AdmmLaunch &a, cudaStream_t stream);
+
+// Schedule of the batched solve: which kernel family and how its work is cut.
+struct Schedule {
+  int family = -1;       // 0: lane groups on plain stage blocks; 2: one thread per stage on halo
+                         // tiles (stage-varying FP32 only); -1: the default for the batch
+  int ctas_per_sm = 0;   // halo tiles: CTAs per SM the shared-memory budget is sized for (0: 2)
+  int item_scale = 0;    // lane groups: sub-chunks per item (0: automatic);
+                         // halo tiles: at most this many tiles per item (0: 4)
+};
+
 // One-thread-per-stage solve (tiled layout, n <= 32).
 int tps_threads();
 int tps_stages_per_subchunk();

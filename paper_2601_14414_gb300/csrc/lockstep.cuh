@@ -39,11 +39,18 @@ struct Args {
   int capI;
 };
 
-// Iterate element (vector b in {z, v, theta, beta, lambda}, component c) of stage k.
-// Plain layout: stage-major with stride n5p. Tiled layout: tiles of 32 stages, element-major
-// inside a tile (one 128-byte line per element for 32 stages in FP32).
-__host__ __device__ inline int64_t iter_index(int tiled, int n, int n5p, int k, int b, int c) {
-  if (tiled) return (int64_t)(k >> 5) * (32 * 5 * n) + (int64_t)(b * n + c) * 32 + (k & 31);
+// Iterate element (vector b in {z, v, theta, beta, lambda}, component c) of stage k (its own
+// copy). Plain layout: stage-major with stride n5p. Tiled layout: tiles of 32 stages,
+// element-major inside a tile (one 128-byte line per element for 32 stages in FP32). Halo
+// tiles: tw slots per tile (see pimpc_internal.cuh).
+__host__ __device__ inline int64_t iter_index(int tiled, int tw, int n, int n5p, int k, int b,
+                                              int c) {
+  if (tiled == 1) return (int64_t)(k >> 5) * (32 * 5 * n) + (int64_t)(b * n + c) * 32 + (k & 31);
+  if (tiled == 2) {
+    int t, s;
+    halo_slot(tw, k, t, s);
+    return (int64_t)t * tile_iter_words(tw, n) + (int64_t)(b * n + c) * tw + s;
+  }
   return (int64_t)k * n5p + b * n + c;
 }
 
@@ -184,6 +191,7 @@ __global__ void prepare_kernel(Args<T> a, int warm, const int *old_base) {
   const int j = blockIdx.y;
   const int n = a.L.nx[j] + a.L.nu[j], N = a.L.N[j];
   const int tiled = a.L.tiled;
+  const int tw = tiled == 2 ? a.L.tw[j] : 0;
   const int n5p = iter_stride_plain(n, (int)sizeof(T));
   const int64_t ib = a.L.Ni[j];
   T *dst = a.it[a.base[j]] + ib;
@@ -192,12 +200,17 @@ __global__ void prepare_kernel(Args<T> a, int warm, const int *old_base) {
        t += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(t / (5 * n)), r = (int)(t - (int64_t)k * 5 * n);
     const int b = r / n, c = r - b * n;
-    const int64_t o = iter_index(tiled, n, n5p, k, b, c);
-    if (warm == 0) {
-      dst[o] = (T)0;
-    } else {
+    T v = (T)0;
+    if (warm != 0) {
       const int ks = k + 1 < N ? k + 1 : N - 1;
-      dst[o] = src[iter_index(tiled, n, n5p, ks, b, c)];
+      v = src[iter_index(tiled, tw, n, n5p, ks, b, c)];
+    }
+    dst[iter_index(tiled, tw, n, n5p, k, b, c)] = v;
+    if (tiled == 2) {  // the copies in the neighbouring tiles' halo slots
+      int tt[2], ss[2];
+      const int m = halo_copies(tw, N, k, tt, ss);
+      for (int q = 0; q < m; ++q)
+        dst[(int64_t)tt[q] * tile_iter_words(tw, n) + (int64_t)(b * n + c) * tw + ss[q]] = v;
     }
   }
 }
@@ -214,7 +227,8 @@ __global__ void output_kernel(Args<T> a, double *u_out, double *x_out) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
-    const double v = (double)z[iter_index(a.L.tiled, n, n5p, k, 0, c)];
+    const int tw = a.L.tiled == 2 ? a.L.tw[j] : 0;
+    const double v = (double)z[iter_index(a.L.tiled, tw, n, n5p, k, 0, c)];
     if (c < nx) {
       if (x_out) x_out[a.L.Nnx[j] + (int64_t)k * nx + c] = v;
     } else if (u_out) {

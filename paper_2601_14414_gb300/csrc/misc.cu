@@ -37,10 +37,12 @@ __global__ void export_kernel(Layout L, T *it0, T *it1, T *it2, const int *base,
   T *bufs[3] = {it0, it1, it2};
   const T *src = bufs[base[j]] + L.Ni[j];
   double *outs[5] = {z, v, th, be, la};
+  const int tw = L.tiled == 2 ? L.tw[j] : 0;
   for (int64_t t = threadIdx.x; t < (int64_t)N * n; t += blockDim.x) {
     const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
     for (int b = 0; b < 5; ++b)
-      if (outs[b]) outs[b][L.Nn[j] + t] = (double)src[ls::iter_index(L.tiled, n, n5p, k, b, c)];
+      if (outs[b])
+        outs[b][L.Nn[j] + t] = (double)src[ls::iter_index(L.tiled, tw, n, n5p, k, b, c)];
   }
 }
 

@@ -9,7 +9,8 @@
 // kernel): [ G_k = [A_k | B_k] : nx rows of stride odd_ld(n) ][ e_k : nx ][ H_k wrapped
 // diagonals ][ M_k wrapped diagonals ], padded to a multiple of 4 elements (W words); an LTV
 // instance has N blocks at blk[j] + k W, an LTI instance two (H_k for k < N-1, then H_{N-1}).
-// Tiled layout (one-thread-per-stage kernel): see admm_tps.cu.
+// Tiled layout (one-thread-per-stage kernel of pimpc_solve_static): see admm_tps.cu.
+// Halo-tile layout (tiled == 2, stage-varying instances, one thread per stage): see below.
 //
 // Iterates (T): three rotating buffers it[0..2]; stage k of instance j holds [z | v | theta | beta |
 // lambda] (5 n values, z = z_{k+1}, padded to a 16-byte multiple n5p) at Ni[j] + n5p k. base[j]
@@ -30,7 +31,8 @@ constexpr int kMaxNLti = 64;
 struct Layout {
   int batch;
   int lti;
-  int tiled;                       // 1: 32-stage tiled layout (n <= 32); 0: plain stage-major
+  int tiled;                       // 0: plain stage-major; 1: 32-stage tiles; 2: halo tiles
+  const int *tw;                   // halo tiles: slots per tile (tiled == 2), else null
   const int *nx, *nu, *N;          // [batch]
   const int64_t *off_nx, *off_nu, *off_n;   // per-instance vector offsets
   const int64_t *Nnx, *Nnu, *Nn;   // per-stage array offsets
@@ -68,6 +70,39 @@ __host__ __device__ inline int block_words(int nx, int nu) {
   return (w + 3) & ~3;
 }
 __host__ __device__ inline int blocks_per_instance(int lti, int N) { return lti ? 2 : N; }
+
+// Halo tiles (tiled == 2). A tile has tw slots (tw <= 32); tile t holds stages t P - 1 .. t P + P
+// in slots 0 .. tw - 1 (P = tw - 2): slots 1 .. P are the tile's own stages, slot 0 repeats the
+// last own stage of tile t - 1 and slot tw - 1 the first own stage of tile t + 1, so that one
+// iteration on a tile reads nothing outside it. Inside a tile every array is element-major:
+// element e of slot s at e * tw + s (one thread per slot reads consecutive words). Stage data
+// (per slot: G = [A | B] row-major nx x n, e, H packed lower row-major, M packed lower) occupies
+// tile_block_words per tile, the iterates (z, v, theta, beta, lambda: 5 n elements per slot)
+// tile_iter_words.
+__host__ __device__ inline int halo_own(int tw) { return tw - 2; }
+__host__ __device__ inline int halo_tiles(int N, int tw) { return (N + tw - 3) / (tw - 2); }
+__host__ __device__ inline int packed_block_words(int nx, int nu) {
+  const int n = nx + nu;
+  return nx * n + nx + packed_size(n) + packed_size(nu);
+}
+__host__ __device__ inline int tile_block_words(int tw, int nx, int nu) {
+  return (tw * packed_block_words(nx, nu) + 3) & ~3;
+}
+__host__ __device__ inline int tile_iter_words(int tw, int n) { return (tw * 5 * n + 3) & ~3; }
+// Tile and slot of stage k's own copy.
+__host__ __device__ inline void halo_slot(int tw, int k, int &t, int &s) {
+  const int P = tw - 2;
+  t = k / P;
+  s = k - t * P + 1;
+}
+// The copies of stage k in neighbouring tiles: (tile, slot) pairs, returns how many (0..2).
+__host__ __device__ inline int halo_copies(int tw, int N, int k, int *tt, int *ss) {
+  int t, s, m = 0;
+  halo_slot(tw, k, t, s);
+  if (s == tw - 2 && t + 1 < halo_tiles(N, tw)) { tt[m] = t + 1; ss[m] = 0; ++m; }
+  if (s == 1 && t >= 1) { tt[m] = t - 1; ss[m] = tw - 1; ++m; }
+  return m;
+}
 
 // Per-instance solver state kept on the device between calls.
 struct InstState {

@@ -7,7 +7,9 @@
 
 struct pimpc_solver {
   int device = 0, batch = 0, lti = 0, prec = 0, tiled = 1;
-  std::vector<int> nx, nu, N, W;
+  std::vector<int> nx, nu, N, W, tw;
+  pimpc::Schedule sched{};
+  std::vector<void *> lay_allocs;   // buffers whose size depends on the schedule
   std::vector<int64_t> off_nx, off_nu, off_n, Nnx, Nnu, Nn, Ni, offA, offB, offe, blk, stage0, bbase;
   int64_t tot_nx = 0, tot_nu = 0, tot_n = 0, tot_Nnx = 0, tot_Nnu = 0, tot_Nn = 0, tot_Ni = 0;
   int64_t tot_A = 0, tot_B = 0, tot_e = 0, tot_blk = 0, nblocks = 0, stage_words = 0;
@@ -49,6 +51,7 @@ struct pimpc_solver {
 
 namespace pimpc {
 int fail(pimpc_solver *s, int code, const std::string &msg);
+int apply_schedule(pimpc_solver *s, const Schedule &sc, std::string &why);
 int cuda_fail(pimpc_solver *s, cudaError_t e, const char *what);
 size_t tsize(int prec);
 cudaError_t dev_in(pimpc_solver *s, const double *p, int64_t count, int mem, int64_t at,

@@ -48,6 +48,9 @@ _SIGS = {
     "pimpc_plant_step": (_I, [_VP, _I, _VP, _D, _VP, _VP, _VP, _I, _VP]),
     "pimpc_backward": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP]),
     "pimpc_solve_static": (_I, [_I, _I, _I, _I] + [_VP] * 11 + [_D, _D, _I, _I, _D] + [_VP] * 6),
+    "pimpc_set_schedule": (_I, [_VP, _I, _I, _I]),
+    "pimpc_get_schedule": (_I, [_VP] * 7),
+    "pimpc_autotune": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -228,6 +231,36 @@ def pimpc_solve_static(nx, nu, N, precision, A, B, e, q, r, xmin, xmax, umin, um
                                            float(eta), *p[11:], st))
 
 
+FAMILY_LANES, FAMILY_TILES = 0, 2
+
+
+def pimpc_set_schedule(h, family, ctas_per_sm=0, item_scale=0):
+    _check(h, load().pimpc_set_schedule(h, int(family), int(ctas_per_sm), int(item_scale)))
+
+
+def pimpc_get_schedule(h):
+    vals = [ctypes.c_int() for _ in range(6)]
+    _check(h, load().pimpc_get_schedule(h, *[ctypes.byref(v) for v in vals]))
+    keys = ("family", "ctas_per_sm", "item_scale", "grid", "threads", "items")
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+def pimpc_autotune(h, trial_iters=20):
+    fam, cps, scale = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    stream = None
+    if load() is not None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+    _check(h, load().pimpc_autotune(h, int(trial_iters), ctypes.byref(fam), ctypes.byref(cps),
+                                    ctypes.byref(scale), ctypes.byref(ms), stream))
+    return dict(family=fam.value, ctas_per_sm=cps.value, item_scale=scale.value, ms=ms.value)
+
+
 # ---- packing of per-instance dicts ----------------------------------------------------------
 
 def _cat(parts):
@@ -297,6 +330,37 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def set_schedule(self, family, ctas_per_sm=0, item_scale=0):
+        pimpc_set_schedule(self.h, family, ctas_per_sm, item_scale)
+
+    def schedule(self):
+        return pimpc_get_schedule(self.h)
+
+    def autotune(self, trial_iters=20, cache=None):
+        """Pick the fastest schedule for this batch (pimpc_autotune). With ``cache`` (a path
+        to a JSON file) a batch with the same signature reuses the stored choice."""
+        key = self.signature()
+        if cache is not None:
+            import json
+            store = json.load(open(cache)) if os.path.exists(cache) else {}
+            if key in store:
+                c = store[key]
+                self.set_schedule(c["family"], c["ctas_per_sm"], c["item_scale"])
+                return dict(c, cached=True)
+        res = pimpc_autotune(self.h, trial_iters)
+        if cache is not None:
+            store[key] = res
+            with open(cache, "w") as f:
+                json.dump(store, f, indent=1, sort_keys=True)
+        return dict(res, cached=False)
+
+    def signature(self):
+        """Autotuner cache key: precision, stage kind, and the multiset of (nx, nu, N bucket)."""
+        import hashlib
+        buckets = sorted(zip(self.nx.tolist(), self.nu.tolist(), (self.N // 64).tolist()))
+        h = hashlib.sha256(repr(buckets).encode()).hexdigest()[:16]
+        return f"p{self.precision}-lti{int(self.lti)}-b{self.batch}-{h}"
 
     def set_options(self, eps, max_iters, accel, eta=0.999, rho=None):
         pimpc_set_options(self.h, self.p["rho"] if rho is None else rho, eps, max_iters, accel, eta)

@@ -1,0 +1,135 @@
+"""Schedules of the batched solve (pimpc_set_schedule / pimpc_autotune) against the FP64 oracle.
+
+Every schedule computes the same iteration: the one-thread-per-stage kernel on halo tiles
+(family 2) must meet the FP32 tolerances of the lane-group kernel (1e-4 on u, x at a fixed
+iteration count, 1e-5 on converged solutions); different item sizes of the lane-group kernel
+change only the order of the sums of c. The batches cover tiles of 32 and 16 slots, instances
+of one tile, several tiles with a ragged last tile, and N = 1.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_14414_gb300 import pimpc
+from paper_2601_14414_gb300 import workloads as W
+from test_gpu_parity import RAGGED, ragged_batch, relerr, solution_error
+
+pytestmark = pytest.mark.gpu
+
+TILE_DIMS = RAGGED + [(24, 8, 45), (3, 2, 95), (2, 1, 2)]
+
+
+def tiles_solver(insts, **kw):
+    s = pimpc.Solver(insts, precision=pimpc.F32, **kw)
+    s.set_schedule(pimpc.FAMILY_TILES)
+    assert s.schedule()["family"] == pimpc.FAMILY_TILES
+    return s
+
+
+def test_halo_tiles_plain_fixed_iterations_match_oracle():
+    insts = ragged_batch(21, dims=TILE_DIMS)
+    s = tiles_solver(insts, eps=-1.0, max_iters=200, accel=0)
+    res = s.solve()
+    ora = oracle.solve_batch(insts, eps=-1.0, max_iters=200, accel=0)
+    for j, o in enumerate(ora):
+        assert relerr(res["u"][j], o["u"]) <= 1e-4, j
+        assert relerr(res["x"][j], o["x"]) <= 1e-4, j
+        assert res["iters"][j] == 200
+
+
+def test_halo_tiles_accel_with_replayed_restarts_matches_oracle():
+    insts = ragged_batch(22, dims=TILE_DIMS)
+    K = 200
+    ora = [oracle.solve(i, eps=-1.0, max_iters=K, accel=1, history=True) for i in insts]
+    mask = np.ascontiguousarray(np.stack([o["mask"] for o in ora]).astype(np.uint8))
+    s = tiles_solver(insts, eps=-1.0, max_iters=K, accel=1)
+    pimpc.pimpc_set_restart_mask(s.h, mask, K)
+    res = s.solve()
+    for j, o in enumerate(ora):
+        assert relerr(res["u"][j], o["u"]) <= 1e-4, j
+        assert relerr(res["x"][j], o["x"]) <= 1e-4, j
+
+
+def test_halo_tiles_converged_match_converged_oracle():
+    insts = ragged_batch(23, dims=[(4, 2, 37), (14, 2, 19), (12, 4, 33), (6, 2, 1), (24, 8, 45)])
+    s = tiles_solver(insts, eps=1e-11, max_iters=20000, accel=1)
+    res = s.solve()
+    ora = oracle.solve_batch(insts, eps=1e-22, max_iters=200000, accel=1)
+    for j, o in enumerate(ora):
+        assert o["status"] == oracle.CONVERGED
+        assert solution_error(res["u"][j], res["x"][j], o["u"], o["x"]) <= 1e-5, j
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_halo_tiles_warm_start(mode):
+    """Warm start reuses (1) or shifts (2) the iterates; the shifted copy must also refresh the
+    halo slots of the neighbouring tiles."""
+    insts = ragged_batch(24, dims=[(4, 2, 70), (24, 8, 45), (14, 2, 19)])
+    s = tiles_solver(insts, eps=-1.0, max_iters=60, accel=0)
+    s.solve()
+    first = s.iterates()
+    res = s.solve(warm_start=mode)
+    for j, inst in enumerate(insts):
+        warm = {k: first[j][k].copy() for k in ("z", "v", "th", "be", "la")}
+        if mode == 2:
+            for k in warm:
+                warm[k] = np.concatenate([warm[k][1:], warm[k][-1:]], axis=0)
+        o = oracle.solve(inst, eps=-1.0, max_iters=60, accel=0, warm=warm)
+        assert relerr(res["u"][j], o["u"]) <= 1e-4, j
+        assert relerr(res["x"][j], o["x"]) <= 1e-4, j
+
+
+def test_lane_group_item_sizes_agree():
+    insts = ragged_batch(25)
+    base = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=120, accel=1).solve()
+    for scale in (1, 3, 40):
+        s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=120, accel=1)
+        s.set_schedule(pimpc.FAMILY_LANES, 0, scale)
+        r = s.solve()
+        for j in range(len(insts)):
+            assert relerr(r["u"][j], base["u"][j]) <= 1e-5
+            assert relerr(r["x"][j], base["x"][j]) <= 1e-5
+
+
+def test_schedule_errors_keep_the_previous_schedule():
+    insts = ragged_batch(26, dims=[(4, 2, 37)])
+    s = pimpc.Solver(insts, precision=pimpc.F64, eps=-1.0, max_iters=50, accel=0)
+    before = s.schedule()
+    with pytest.raises(pimpc.PimpcError) as e:
+        s.set_schedule(pimpc.FAMILY_TILES)        # halo tiles are FP32 only
+    assert e.value.code == pimpc.EINVAL
+    assert s.schedule() == before
+    with pytest.raises(pimpc.PimpcError):
+        s.set_schedule(7)
+    o = oracle.solve(insts[0], eps=-1.0, max_iters=50, accel=0)
+    r = s.solve()
+    assert relerr(r["u"][0], o["u"]) <= 1e-10
+
+
+def test_autotune_picks_a_schedule_that_solves_correctly(tmp_path):
+    insts = ragged_batch(27, dims=TILE_DIMS)
+    s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=150, accel=0)
+    pick = s.autotune(trial_iters=10, cache=str(tmp_path / "tune.json"))
+    assert pick["family"] in (pimpc.FAMILY_LANES, pimpc.FAMILY_TILES) and pick["ms"] > 0
+    assert s.schedule()["family"] == pick["family"] and not pick["cached"]
+    again = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=150, accel=0)
+    assert again.autotune(cache=str(tmp_path / "tune.json"))["cached"]
+    res = s.solve()
+    ora = oracle.solve_batch(insts, eps=-1.0, max_iters=150, accel=0)
+    for j, o in enumerate(ora):
+        assert relerr(res["u"][j], o["u"]) <= 1e-4
+        assert relerr(res["x"][j], o["x"]) <= 1e-4
+
+
+def test_adjoint_on_halo_tiles():
+    from test_gpu_adjoint import NAMES, fd, loss_weights, small_batch
+    insts = small_batch()
+    Wu, Wx = loss_weights(insts, seed=2)
+    s = tiles_solver(insts, eps=-1.0, max_iters=40, accel=0)
+    s.solve()
+    g = s.backward(Wu, Wx, checkpoint_every=10)
+    for j, inst in enumerate(insts):
+        for name in NAMES:
+            ref = fd(inst, Wu[j], Wx[j], 40, name)
+            got = np.asarray(g[name][j]).reshape(ref.shape)
+            assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, float(np.max(np.abs(ref)))), name
