@@ -165,6 +165,19 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
                 double *c, int *status, int mem, void *stream);
 
 /*
+ * pimpc_set_polish -- FP64 polish of FP32 solves: after the FP32 iterations stop (eps or
+ * max_iters), up to polish_iters further iterations run in FP64 (FP64 stage cache, FP64 residual
+ * c) from the FP32 iterates, stopping on c <= polish_eps; u_out and x_out are then the polished
+ * FP64 results and the per-instance iters, c and status of pimpc_solve / pimpc_get_stats are
+ * (FP32 iterations + polish iterations, the polish's c, the polish's status). polish_iters = 0
+ * (the default) turns it off; solvers with FP64 iterations ignore it. The first polished solve
+ * creates an FP64 copy of the stage cache and iterate buffers (about twice the FP32 memory).
+ * pimpc_get_iterates keeps returning the FP32 iterates, and warm starts reuse them.
+ * Errors: PIMPC_EINVAL (polish_iters < 0, NaN polish_eps).
+ */
+int pimpc_set_polish(pimpc_solver *s, int polish_iters, double polish_eps);
+
+/*
  * pimpc_get_iterates -- copy the iterates the last solve ended with (the non-hat iterates that
  * Algorithm 1 outputs for warm start): z, v, theta, beta, lambda, each [sum N n], with
  * z[k] = z_{k+1}, v[k] = v_k, theta[k] = theta_k, ... Any pointer may be NULL.

@@ -478,6 +478,8 @@ extern "C" int pimpc_backward(pimpc_solver *s, const double *dL_du, const double
   if (mem != PIMPC_HOST && mem != PIMPC_DEVICE) return fail(s, PIMPC_EINVAL, "bad mem");
   if (checkpoint_every < 1) return fail(s, PIMPC_EINVAL, "checkpoint_every must be >= 1");
   if (!s->solved) return fail(s, PIMPC_ESTATE, "no solve has run");
+  if (s->last_polished)
+    return fail(s, PIMPC_ESTATE, "the last solve ran an FP64 polish; the adjoint covers one precision");
   if (s->last_warm != 0 || s->last_accel != 0 || s->last_eps >= 0.0)
     return fail(s, PIMPC_ESTATE,
                 "the last solve must use warm_start = 0, accel = 0 and eps < 0 (fixed iterations)");

@@ -18,6 +18,10 @@ using namespace pimpc;
 namespace pimpc {
 cudaError_t launch_unpack_state(const InstState *st, int batch, int *iters, double *c,
                                 int *status, int *momentum, cudaStream_t stream);
+cudaError_t launch_copy_iterates(const Layout &Ls, void *const *its, const int *base_s, int prec_s,
+                                 const Layout &Ld, void *const *itd, const int *base_d,
+                                 cudaStream_t stream);
+cudaError_t launch_add_state(InstState *st, const InstState *polish, int batch, cudaStream_t stream);
 cudaError_t launch_fill(double *dst, int64_t count, double value, cudaStream_t stream);
 }  // namespace pimpc
 
@@ -319,6 +323,92 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
 
 }  // namespace pimpc
 
+namespace {
+
+// One solve on FP64 device inputs: the stage cache if stale, xbar_0 and the reference in the
+// iteration precision, then the persistent launch; u_dev, x_dev (device, may be null) receive
+// the outputs.
+int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const double *dref,
+              int ref_per_stage, int warm_start, double *u_dev, double *x_dev, cudaStream_t st) {
+  if (s->stale) {
+    const int rc = pimpc_factorise(s, st);
+    if (rc) return rc;
+  }
+  if (!s->solved) warm_start = 0;  // nothing to reuse after a new schedule
+  const int64_t nref = ref_per_stage ? s->tot_Nn : s->tot_n;
+  PIMPC_CHECK(s, launch_gather_n(s->L, dx0, dup, s->tot_n, s->prec, s->xb0_T, st), "x0");
+  if (dref) PIMPC_CHECK(s, launch_convert(dref, nref, s->prec, s->ref_T, st), "ref");
+  AdmmLaunch a = s->plan;
+  a.L = s->L; a.blk = s->blk_T;
+  for (int b = 0; b < 3; ++b) a.it[b] = s->it[b];
+  a.qd = s->qd_T; a.ref = dref ? s->ref_T : nullptr; a.ref_per_stage = ref_per_stage;
+  a.lo = s->lo_T; a.hi = s->hi_T; a.xb0 = s->xb0_T;
+  a.rho = s->rho; a.eps = s->eps; a.eta = s->eta; a.max_iters = s->max_iters; a.accel = s->accel;
+  a.mask = s->mask; a.mask_len = s->mask_len;
+  a.item_inst = s->item_inst; a.item_a = s->item_a; a.item_b = s->item_b;
+  a.nitems_inst = s->nitems_inst; a.nitems = s->nitems;
+  a.list0 = s->list0; a.list1 = s->list1; a.ctl = s->ctl;
+  a.base = s->base; a.old_base = s->old_base; a.st = s->st;
+  a.alpha = s->alpha; a.cprev = s->cprev; a.coef = s->coef; a.cacc = s->cacc;
+  a.ndone = s->ndone; a.stop = s->stop;
+  a.warm = warm_start;
+  a.u_out = u_dev;
+  a.x_out = x_dev;
+  PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st) : launch_admm(a, s->prec, st), "solve");
+  s->solved = true;
+  s->last_ref_per_stage = ref_per_stage;
+  s->last_ref_given = dref != nullptr;
+  s->last_warm = warm_start;
+  s->last_accel = s->accel;
+  s->last_eps = s->eps;
+  s->last_iters_fixed = s->max_iters;
+  return PIMPC_OK;
+}
+
+// FP64 polish after an FP32 solve: FP64 iterations (the FP64 stage cache, FP64 residual c)
+// started from the FP32 iterates, run by an FP64 solver object that reads this solver's FP64
+// dynamics, weights and bounds. Per-instance results become the sum of both iteration counts
+// and the polish's c and status.
+int run_polish(pimpc_solver *s, const double *dx0, const double *dup, const double *dref,
+               int ref_per_stage, double *u_dev, double *x_dev, cudaStream_t st) {
+  if (!s->shadow) {
+    pimpc_solver *sh = nullptr;
+    const int rc = pimpc_create(s->batch, s->nx.data(), s->nu.data(), s->N.data(), s->lti,
+                                PIMPC_F64, s->device, &sh);
+    if (rc != PIMPC_OK) return fail(s, rc, std::string("polish solver: ") + pimpc_last_error(nullptr));
+    s->shadow = sh;
+    s->shadow_fgen = -1;
+  }
+  pimpc_solver *sh = s->shadow;
+  sh->rho = s->rho;
+  sh->eps = s->polish_eps;
+  sh->max_iters = s->polish_iters;
+  sh->accel = s->accel;
+  sh->eta = s->eta;
+  const size_t nb = sizeof(double) * s->tot_n;
+  PIMPC_CHECK(s, cudaMemcpyAsync(sh->qd_T, s->qd64, nb, cudaMemcpyDeviceToDevice, st), "polish weights");
+  PIMPC_CHECK(s, cudaMemcpyAsync(sh->lo_T, s->lo64, nb, cudaMemcpyDeviceToDevice, st), "polish bounds");
+  PIMPC_CHECK(s, cudaMemcpyAsync(sh->hi_T, s->hi64, nb, cudaMemcpyDeviceToDevice, st), "polish bounds");
+  if (s->shadow_fgen != s->fgen) {
+    PIMPC_CHECK(s, launch_factorise(sh->L, s->A64, s->B64, s->e64, s->qd64,
+                                    s->have_rdu ? s->rdu64 : nullptr, s->rho, sh->binst,
+                                    sh->d_bbase, sh->nblocks, sh->max_nx, sh->max_n, PIMPC_F64,
+                                    sh->blk_T, sh->ferr, st),
+                "polish factorise");
+    s->shadow_fgen = s->fgen;
+  }
+  sh->stale = false;
+  sh->solved = true;
+  PIMPC_CHECK(s, launch_copy_iterates(s->L, s->it, s->base, s->prec, sh->L, sh->it, sh->base, st),
+              "polish start");
+  const int rc = run_solve(sh, dx0, dup, dref, ref_per_stage, 1, u_dev, x_dev, st);
+  if (rc != PIMPC_OK) return fail(s, rc, std::string("polish: ") + sh->err);
+  PIMPC_CHECK(s, launch_add_state(s->st, sh->st, s->batch, st), "polish state");
+  return PIMPC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *pimpc_last_error(const pimpc_solver *s) {
@@ -332,6 +422,7 @@ void pimpc_destroy(pimpc_solver *s) {
   for (void *p : s->allocs) cudaFree(p);
   for (void *p : s->lay_allocs) cudaFree(p);
   if (s->adj_ws) cudaFree(s->adj_ws);
+  if (s->shadow) pimpc_destroy(s->shadow);
   if (s->mask_alloc) cudaFree(s->mask_alloc);
   delete s;
 }
@@ -425,6 +516,8 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(dalloc(s, &s->lo_T, ts * s->tot_n));
   chk(dalloc(s, &s->hi_T, ts * s->tot_n));
   chk(dalloc(s, &s->xb0_T, ts * s->tot_n));
+  chk(dalloc(s, &s->lo64, sizeof(double) * s->tot_n));
+  chk(dalloc(s, &s->hi64, sizeof(double) * s->tot_n));
   chk(dalloc(s, &s->base, sizeof(int) * batch));
   chk(dalloc(s, &s->old_base, sizeof(int) * batch));
   chk(dalloc(s, &s->alpha, sizeof(double) * batch));
@@ -455,11 +548,11 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(cudaMemset(s->st, 0, sizeof(InstState) * batch));
   {
     std::vector<double> inf(s->tot_n, INFINITY);
-    chk(cudaMemcpy(s->stage64, inf.data(), sizeof(double) * s->tot_n, cudaMemcpyHostToDevice));
-    chk(launch_convert(s->stage64, s->tot_n, precision, s->hi_T, 0));
+    chk(cudaMemcpy(s->hi64, inf.data(), sizeof(double) * s->tot_n, cudaMemcpyHostToDevice));
+    chk(launch_convert(s->hi64, s->tot_n, precision, s->hi_T, 0));
     for (auto &v : inf) v = -INFINITY;
-    chk(cudaMemcpy(s->stage64, inf.data(), sizeof(double) * s->tot_n, cudaMemcpyHostToDevice));
-    chk(launch_convert(s->stage64, s->tot_n, precision, s->lo_T, 0));
+    chk(cudaMemcpy(s->lo64, inf.data(), sizeof(double) * s->tot_n, cudaMemcpyHostToDevice));
+    chk(launch_convert(s->lo64, s->tot_n, precision, s->lo_T, 0));
     chk(cudaDeviceSynchronize());
   }
   if (e != cudaSuccess) {
@@ -493,7 +586,10 @@ int pimpc_set_options(pimpc_solver *s, double rho, double eps, int max_iters, in
   if (accel != 0 && accel != 1) return fail(s, PIMPC_EINVAL, "accel must be 0 or 1");
   if (!(eta >= 0.0) || !std::isfinite(eta)) return fail(s, PIMPC_EINVAL, "eta must be >= 0");
   if (s->mask && s->mask_len > max_iters) return fail(s, PIMPC_EINVAL, "restart mask longer than max_iters");
-  if (rho != s->rho) s->stale = true;
+  if (rho != s->rho) {
+    s->stale = true;
+    ++s->fgen;
+  }
   s->rho = rho; s->eps = eps; s->max_iters = max_iters; s->accel = accel; s->eta = eta;
   return PIMPC_OK;
 }
@@ -521,6 +617,7 @@ int pimpc_set_weights(pimpc_solver *s, const double *q, const double *r, const d
   PIMPC_CHECK(s, launch_gather_n64(s->L, nullptr, drdu, s->tot_n, s->rdu64, st), "weights");
   s->have_rdu = rdu != nullptr;
   s->stale = true;
+  ++s->fgen;
   if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "set_weights");
   return PIMPC_OK;
 }
@@ -547,6 +644,8 @@ int pimpc_set_bounds(pimpc_solver *s, const double *xmin, const double *xmax, co
   PIMPC_CHECK(s, dev_in(s, umax, s->tot_nu, mem, o, st, &d), "copy bounds");
   PIMPC_CHECK(s, launch_gather_n(s->L, a, c, s->tot_n, s->prec, s->lo_T, st), "bounds");
   PIMPC_CHECK(s, launch_gather_n(s->L, b, d, s->tot_n, s->prec, s->hi_T, st), "bounds");
+  PIMPC_CHECK(s, launch_gather_n64(s->L, a, c, s->tot_n, s->lo64, st), "bounds");
+  PIMPC_CHECK(s, launch_gather_n64(s->L, b, d, s->tot_n, s->hi64, st), "bounds");
   if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "set_bounds");
   return PIMPC_OK;
 }
@@ -562,6 +661,7 @@ int pimpc_set_dynamics(pimpc_solver *s, const double *A, const double *B, const 
   if (e) PIMPC_CHECK(s, cudaMemcpyAsync(s->e64, e, sizeof(double) * s->tot_e, kind, st), "copy e");
   else PIMPC_CHECK(s, cudaMemsetAsync(s->e64, 0, sizeof(double) * s->tot_e, st), "zero e");
   s->stale = true;
+  ++s->fgen;
   if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "set_dynamics");
   return PIMPC_OK;
 }
@@ -586,6 +686,7 @@ int pimpc_linearise(pimpc_solver *s, int model, const double *params, double dt,
                                   s->lti ? nullptr : s->binst, s->lti ? nullptr : s->d_bbase, st),
               "linearise");
   s->stale = true;
+  ++s->fgen;
   if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "linearise");
   return PIMPC_OK;
 }
@@ -614,6 +715,15 @@ int pimpc_factorise(pimpc_solver *s, void *stream) {
   return PIMPC_OK;
 }
 
+int pimpc_set_polish(pimpc_solver *s, int polish_iters, double polish_eps) {
+  if (!s) return PIMPC_EINVAL;
+  if (polish_iters < 0) return fail(s, PIMPC_EINVAL, "polish_iters < 0");
+  if (std::isnan(polish_eps)) return fail(s, PIMPC_EINVAL, "polish_eps is NaN");
+  s->polish_iters = polish_iters;
+  s->polish_eps = polish_eps;
+  return PIMPC_OK;
+}
+
 int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const double *ref,
                 int ref_per_stage, int warm_start, double *u_out, double *x_out, int *iters,
                 double *c, int *status, int mem, void *stream) {
@@ -622,42 +732,23 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
   if (ref_per_stage != 0 && ref_per_stage != 1) return fail(s, PIMPC_EINVAL, "ref_per_stage must be 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   cudaSetDevice(s->device);
-  if (s->stale) {
-    int rc = pimpc_factorise(s, stream);
-    if (rc) return rc;
-  }
   const double *dx0, *dup, *dref;
   const int64_t nref = ref_per_stage ? s->tot_Nn : s->tot_n;
   PIMPC_CHECK(s, dev_in(s, x0, s->tot_nx, mem, 0, st, &dx0), "copy x0");
   PIMPC_CHECK(s, dev_in(s, u_prev, s->tot_nu, mem, s->tot_nx, st, &dup), "copy u_prev");
   PIMPC_CHECK(s, dev_in(s, ref, nref, mem, s->tot_nx + s->tot_nu, st, &dref), "copy ref");
-  PIMPC_CHECK(s, launch_gather_n(s->L, dx0, dup, s->tot_n, s->prec, s->xb0_T, st), "x0");
-  if (dref) PIMPC_CHECK(s, launch_convert(dref, nref, s->prec, s->ref_T, st), "ref");
-  AdmmLaunch a = s->plan;
-  a.L = s->L; a.blk = s->blk_T;
-  for (int b = 0; b < 3; ++b) a.it[b] = s->it[b];
-  a.qd = s->qd_T; a.ref = dref ? s->ref_T : nullptr; a.ref_per_stage = ref_per_stage;
-  a.lo = s->lo_T; a.hi = s->hi_T; a.xb0 = s->xb0_T;
-  a.rho = s->rho; a.eps = s->eps; a.eta = s->eta; a.max_iters = s->max_iters; a.accel = s->accel;
-  a.mask = s->mask; a.mask_len = s->mask_len;
-  a.item_inst = s->item_inst; a.item_a = s->item_a; a.item_b = s->item_b;
-  a.nitems_inst = s->nitems_inst; a.nitems = s->nitems;
-  a.list0 = s->list0; a.list1 = s->list1; a.ctl = s->ctl;
-  a.base = s->base; a.old_base = s->old_base; a.st = s->st;
-  a.alpha = s->alpha; a.cprev = s->cprev; a.coef = s->coef; a.cacc = s->cacc;
-  a.ndone = s->ndone; a.stop = s->stop;
-  a.warm = warm_start;
   const bool dev = mem == PIMPC_DEVICE;
-  a.u_out = u_out ? (dev ? u_out : s->out_u) : nullptr;
-  a.x_out = x_out ? (dev ? x_out : s->out_x) : nullptr;
-  PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st) : launch_admm(a, s->prec, st), "solve");
-  s->solved = true;
-  s->last_ref_per_stage = ref_per_stage;
-  s->last_ref_given = dref != nullptr;
-  s->last_warm = warm_start;
-  s->last_accel = s->accel;
-  s->last_eps = s->eps;
-  s->last_iters_fixed = s->max_iters;
+  double *u_dev = u_out ? (dev ? u_out : s->out_u) : nullptr;
+  double *x_dev = x_out ? (dev ? x_out : s->out_x) : nullptr;
+  const bool polish = s->polish_iters > 0 && s->prec == PIMPC_F32;
+  int rc = run_solve(s, dx0, dup, dref, ref_per_stage, warm_start, polish ? nullptr : u_dev,
+                     polish ? nullptr : x_dev, st);
+  if (rc != PIMPC_OK) return rc;
+  if (polish) {
+    rc = run_polish(s, dx0, dup, dref, ref_per_stage, u_dev, x_dev, st);
+    if (rc != PIMPC_OK) return rc;
+  }
+  s->last_polished = polish;
   if (dev) {
     if (iters || c || status)
       PIMPC_CHECK(s, launch_unpack_state(s->st, s->batch, iters, c, status, nullptr, st), "state");

@@ -105,6 +105,37 @@ __global__ void unpack_state_kernel(const InstState *st, int batch, int *iters, 
   if (momentum) momentum[j] = st[j].momentum;
 }
 
+// Iterates of the latest buffer of one layout (iteration type S) -> the latest buffer of a
+// plain FP64 layout (the polish's starting point); one block per instance.
+template <typename S>
+__global__ void copy_iterates_kernel(Layout Ls, const S *s0, const S *s1, const S *s2,
+                                     const int *base_s, Layout Ld, double *d0, double *d1,
+                                     double *d2, const int *base_d) {
+  const int j = blockIdx.x;
+  const int n = Ls.nx[j] + Ls.nu[j], N = Ls.N[j];
+  const S *srcs[3] = {s0, s1, s2};
+  double *dsts[3] = {d0, d1, d2};
+  const S *src = srcs[base_s[j]] + Ls.Ni[j];
+  double *dst = dsts[base_d[j]] + Ld.Ni[j];
+  const int n5s = ls::iter_stride_plain(n, (int)sizeof(S)), n5d = ls::iter_stride_plain(n, 8);
+  const int tws = Ls.tiled == 2 ? Ls.tw[j] : 0;
+  for (int64_t t = threadIdx.x; t < (int64_t)N * 5 * n; t += blockDim.x) {
+    const int k = (int)(t / (5 * n)), r = (int)(t - (int64_t)k * 5 * n);
+    const int b = r / n, c = r - b * n;
+    dst[ls::iter_index(Ld.tiled, 0, n, n5d, k, b, c)] =
+        (double)src[ls::iter_index(Ls.tiled, tws, n, n5s, k, b, c)];
+  }
+}
+
+__global__ void add_state_kernel(InstState *st, const InstState *polish, int batch) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= batch) return;
+  st[j].iters += polish[j].iters;
+  st[j].momentum += polish[j].momentum;
+  st[j].c = polish[j].c;
+  st[j].status = polish[j].status;
+}
+
 __global__ void fill_kernel(double *dst, int64_t count, double value) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -117,6 +148,26 @@ cudaError_t launch_unpack_state(const InstState *st, int batch, int *iters, doub
                                 int *status, int *momentum, cudaStream_t stream) {
   unpack_state_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(st, batch, iters, c, status,
                                                                momentum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_iterates(const Layout &Ls, void *const *its, const int *base_s, int prec_s,
+                                 const Layout &Ld, void *const *itd, const int *base_d,
+                                 cudaStream_t stream) {
+  double *const *d = reinterpret_cast<double *const *>(itd);
+  if (prec_s == 0)
+    copy_iterates_kernel<float><<<Ls.batch, 256, 0, stream>>>(
+        Ls, (const float *)its[0], (const float *)its[1], (const float *)its[2], base_s, Ld, d[0],
+        d[1], d[2], base_d);
+  else
+    copy_iterates_kernel<double><<<Ls.batch, 256, 0, stream>>>(
+        Ls, (const double *)its[0], (const double *)its[1], (const double *)its[2], base_s, Ld,
+        d[0], d[1], d[2], base_d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_state(InstState *st, const InstState *polish, int batch, cudaStream_t stream) {
+  add_state_kernel<<<(batch + 127) / 128, 128, 0, stream>>>(st, polish, batch);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,14 @@ struct pimpc_solver {
   int grid_admm = 0;
   pimpc::AdmmLaunch plan{};
   std::string err;
+  // FP64 polish: FP64 bounds, options, and the FP64 solver that runs the polish iterations
+  // (created by the first polished solve; it reads this solver's FP64 dynamics and weights)
+  double *lo64 = nullptr, *hi64 = nullptr;
+  int polish_iters = 0;
+  double polish_eps = 0.0;
+  pimpc_solver *shadow = nullptr;
+  long fgen = 0, shadow_fgen = -1;   // generation of the factorisation inputs
+  bool last_polished = false;
   // adjoint workspace (allocated by the first pimpc_backward)
   void *adj_ws = nullptr;
   size_t adj_ws_bytes = 0;

@@ -49,6 +49,7 @@ _SIGS = {
     "pimpc_backward": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP]),
     "pimpc_solve_static": (_I, [_I, _I, _I, _I] + [_VP] * 11 + [_D, _D, _I, _I, _D] + [_VP] * 6),
     "pimpc_set_schedule": (_I, [_VP, _I, _I, _I]),
+    "pimpc_set_polish": (_I, [_VP, _I, _D]),
     "pimpc_get_schedule": (_I, [_VP] * 7),
     "pimpc_autotune": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP]),
 }
@@ -234,6 +235,10 @@ def pimpc_solve_static(nx, nu, N, precision, A, B, e, q, r, xmin, xmax, umin, um
 FAMILY_LANES, FAMILY_TILES = 0, 2
 
 
+def pimpc_set_polish(h, polish_iters, polish_eps=0.0):
+    _check(h, load().pimpc_set_polish(h, int(polish_iters), float(polish_eps)))
+
+
 def pimpc_set_schedule(h, family, ctas_per_sm=0, item_scale=0):
     _check(h, load().pimpc_set_schedule(h, int(family), int(ctas_per_sm), int(item_scale)))
 
@@ -330,6 +335,9 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def set_polish(self, polish_iters, polish_eps=0.0):
+        pimpc_set_polish(self.h, polish_iters, polish_eps)
 
     def set_schedule(self, family, ctas_per_sm=0, item_scale=0):
         pimpc_set_schedule(self.h, family, ctas_per_sm, item_scale)

@@ -253,3 +253,49 @@ def test_device_memory_calls_match_host_calls():
     np.testing.assert_array_equal(u.cpu().numpy(), np.concatenate([a.ravel() for a in host["u"]]))
     np.testing.assert_array_equal(x.cpu().numpy(), np.concatenate([a.ravel() for a in host["x"]]))
     assert it.cpu().numpy().tolist() == [50, 50]
+
+
+# ---- FP64 polish of FP32 solves -------------------------------------------------------------
+
+POLISH_DIMS = [(4, 2, 37), (14, 2, 19), (12, 4, 33), (6, 2, 1), (9, 9, 17), (24, 8, 45)]
+
+
+@pytest.mark.parametrize("family", [pimpc.FAMILY_LANES, pimpc.FAMILY_TILES])
+def test_fp64_polish_reaches_the_fp64_solution(family):
+    """FP32 iterations to eps = 1e-8, then FP64 iterations to 1e-22: the result must match the
+    converged FP64 oracle to 1e-9, far below what FP32 iterations alone reach (about 1e-6)."""
+    insts = ragged_batch(31, dims=POLISH_DIMS)
+    s = pimpc.Solver(insts, precision=pimpc.F32, eps=1e-8, max_iters=20000, accel=1)
+    if family == pimpc.FAMILY_TILES:
+        s.set_schedule(family)
+    plain = s.solve()
+    s.set_polish(200000, 1e-22)
+    res = s.solve()
+    ora = oracle_runs(insts, eps=1e-22, max_iters=200000, accel=1)
+    for j, o in enumerate(ora):
+        assert o["status"] == oracle.CONVERGED
+        assert res["status"][j] == pimpc.CONVERGED and res["c"][j] <= 1e-22
+        assert res["iters"][j] > plain["iters"][j]        # FP32 iterations + polish iterations
+        assert solution_error(res["u"][j], res["x"][j], o["u"], o["x"]) <= 1e-9, j
+
+
+def test_polish_is_ignored_by_fp64_solvers_and_refused_by_the_adjoint():
+    insts = ragged_batch(32, dims=POLISH_DIMS[:2])
+    s = pimpc.Solver(insts, precision=pimpc.F64, eps=-1.0, max_iters=50, accel=0)
+    a = s.solve()
+    s.set_polish(100, 1e-20)
+    b = s.solve()
+    for j in range(len(insts)):
+        assert np.array_equal(a["u"][j], b["u"][j]) and b["iters"][j] == 50
+    f = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=50, accel=0)
+    f.set_polish(10, -1.0)
+    r = f.solve()
+    assert all(it == 60 for it in r["iters"])
+    gu = [np.ones((i["N"], i["nu"])) for i in insts]
+    gx = [np.ones((i["N"], i["nx"])) for i in insts]
+    with pytest.raises(pimpc.PimpcError) as e:
+        f.backward(gu, gx)
+    assert e.value.code == pimpc.ESTATE
+    with pytest.raises(pimpc.PimpcError) as e:
+        f.set_polish(-1)
+    assert e.value.code == pimpc.EINVAL
