@@ -165,6 +165,27 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
                 double *c, int *status, int mem, void *stream);
 
 /*
+ * pimpc_set_graph -- CUDA graphs for device-memory solves (enable = 1) or direct launches
+ * (enable = 0, the default). With graphs on, the launches of a pimpc_solve with mem ==
+ * PIMPC_DEVICE are recorded into a CUDA graph the first time an argument set (the pointers,
+ * ref_per_stage, warm_start, polish on or off) is seen and replayed by later calls with the same
+ * set: one graph launch per solve. The stage cache, when stale, is rebuilt outside the graph
+ * before the launch. A call that changes launch parameters (set_options, set_schedule,
+ * set_polish, set_restart_mask) drops the recorded graphs. If the driver refuses the capture,
+ * that call and later ones run the launches directly (pimpc_get_graph_stats reports why).
+ * Host-memory solves always launch directly. Errors: PIMPC_EINVAL.
+ */
+int pimpc_set_graph(pimpc_solver *s, int enable);
+
+/*
+ * pimpc_get_graph_stats -- whether graphs are in use, how many graphs were captured and how
+ * many solves replayed one, and (when the capture was refused) the driver's reason (owned by the
+ * solver, valid until the next call on it; NULL otherwise). Any pointer may be NULL.
+ */
+int pimpc_get_graph_stats(pimpc_solver *s, int *enabled, long long *captures, long long *replays,
+                          const char **refused);
+
+/*
  * pimpc_set_polish -- FP64 polish of FP32 solves: after the FP32 iterations stop (eps or
  * max_iters), up to polish_iters further iterations run in FP64 (FP64 stage cache, FP64 residual
  * c) from the FP32 iterates, stopping on c <= polish_eps; u_out and x_out are then the polished

@@ -38,6 +38,11 @@ int fail(pimpc_solver *s, int code, const std::string &msg) {
   return code;
 }
 
+void graph_invalidate(pimpc_solver *s) {
+  for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
 int cuda_fail(pimpc_solver *s, cudaError_t e, const char *what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
   return fail(s, PIMPC_ECUDA, m);
@@ -260,6 +265,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
 
   // (Re)allocate and upload what depends on the schedule.
   cudaDeviceSynchronize();
+  graph_invalidate(s);
   free_layout(s);
   e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
@@ -369,8 +375,9 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
 // started from the FP32 iterates, run by an FP64 solver object that reads this solver's FP64
 // dynamics, weights and bounds. Per-instance results become the sum of both iteration counts
 // and the polish's c and status.
-int run_polish(pimpc_solver *s, const double *dx0, const double *dup, const double *dref,
-               int ref_per_stage, double *u_dev, double *x_dev, cudaStream_t st) {
+// Host-side and eager part of the polish: the FP64 solver, its options, weights, bounds and (if
+// the inputs changed) its stage cache.
+int prepare_polish(pimpc_solver *s, cudaStream_t st) {
   if (!s->shadow) {
     pimpc_solver *sh = nullptr;
     const int rc = pimpc_create(s->batch, s->nx.data(), s->nu.data(), s->N.data(), s->lti,
@@ -399,11 +406,91 @@ int run_polish(pimpc_solver *s, const double *dx0, const double *dup, const doub
   }
   sh->stale = false;
   sh->solved = true;
+  return PIMPC_OK;
+}
+
+// The launches of the polish (capturable): FP32 iterates -> FP64 start, FP64 solve, results.
+int polish_launch(pimpc_solver *s, const double *dx0, const double *dup, const double *dref,
+                  int ref_per_stage, double *u_dev, double *x_dev, cudaStream_t st) {
+  pimpc_solver *sh = s->shadow;
   PIMPC_CHECK(s, launch_copy_iterates(s->L, s->it, s->base, s->prec, sh->L, sh->it, sh->base, st),
               "polish start");
   const int rc = run_solve(sh, dx0, dup, dref, ref_per_stage, 1, u_dev, x_dev, st);
   if (rc != PIMPC_OK) return fail(s, rc, std::string("polish: ") + sh->err);
   PIMPC_CHECK(s, launch_add_state(s->st, sh->st, s->batch, st), "polish state");
+  return PIMPC_OK;
+}
+
+// Device-memory solve through a CUDA graph: the launches of one solve (x0 and reference
+// conversion, the per-instance reset, the starting iterates, the persistent cooperative kernel,
+// the outputs, the polish and the status unpacking) are captured once per argument set and
+// replayed by later calls with the same arguments; the stage cache (when stale) and the
+// polish's host-side preparation run before, outside the graph. A refused capture sets
+// graph_failed and leaves the caller to run the launches directly.
+int graph_solve(pimpc_solver *s, const double *dx0, const double *dup, const double *dref,
+                int ref_per_stage, int warm_start, double *u_dev, double *x_dev, int *iters,
+                double *c, int *status, bool polish, cudaStream_t st) {
+  if (s->stale) {
+    const int rc = pimpc_factorise(s, st);
+    if (rc) return rc;
+  }
+  if (polish) {
+    const int rc = prepare_polish(s, st);
+    if (rc) return rc;
+  }
+  const int warm = s->solved ? warm_start : 0;
+  const std::vector<uintptr_t> key = {
+      (uintptr_t)dx0, (uintptr_t)dup, (uintptr_t)dref, (uintptr_t)ref_per_stage, (uintptr_t)warm,
+      (uintptr_t)u_dev, (uintptr_t)x_dev, (uintptr_t)iters, (uintptr_t)c, (uintptr_t)status,
+      (uintptr_t)polish};
+  pimpc_solver::GraphEntry *hit = nullptr;
+  for (auto &g : s->graphs)
+    if (g.key == key) hit = &g;
+  if (!hit) {
+    if (!s->cap_stream) PIMPC_CHECK(s, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "capture stream");
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = PIMPC_OK;
+    if (e == cudaSuccess) {
+      rc = run_solve(s, dx0, dup, dref, ref_per_stage, warm, polish ? nullptr : u_dev,
+                     polish ? nullptr : x_dev, s->cap_stream);
+      if (rc == PIMPC_OK && polish)
+        rc = polish_launch(s, dx0, dup, dref, ref_per_stage, u_dev, x_dev, s->cap_stream);
+      if (rc == PIMPC_OK && (iters || c || status)) {
+        const cudaError_t e3 = launch_unpack_state(s->st, s->batch, iters, c, status, nullptr, s->cap_stream);
+        if (e3 != cudaSuccess) rc = cuda_fail(s, e3, "state");
+      }
+      const cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && rc == PIMPC_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || rc != PIMPC_OK) {
+      s->graph_failed = 1;
+      s->graph_err = e != cudaSuccess ? cudaGetErrorString(e) : s->err;
+      (void)cudaGetLastError();
+      return PIMPC_OK;
+    }
+    if (s->graphs.size() >= 8) {
+      cudaGraphExecDestroy(s->graphs.front().exec);
+      s->graphs.erase(s->graphs.begin());
+    }
+    s->graphs.push_back({key, exec, warm, ref_per_stage, dref != nullptr, polish ? 1 : 0});
+    hit = &s->graphs.back();
+    ++s->graph_captures;
+  } else {
+    ++s->graph_replays;
+  }
+  PIMPC_CHECK(s, cudaGraphLaunch(hit->exec, st), "graph launch");
+  s->solved = true;
+  s->last_ref_per_stage = hit->ref_per_stage;
+  s->last_ref_given = hit->ref_given;
+  s->last_warm = hit->warm;
+  s->last_accel = s->accel;
+  s->last_eps = s->eps;
+  s->last_iters_fixed = s->max_iters;
+  s->last_polished = hit->polished != 0;
   return PIMPC_OK;
 }
 
@@ -423,6 +510,8 @@ void pimpc_destroy(pimpc_solver *s) {
   for (void *p : s->lay_allocs) cudaFree(p);
   if (s->adj_ws) cudaFree(s->adj_ws);
   if (s->shadow) pimpc_destroy(s->shadow);
+  graph_invalidate(s);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->mask_alloc) cudaFree(s->mask_alloc);
   delete s;
 }
@@ -591,6 +680,7 @@ int pimpc_set_options(pimpc_solver *s, double rho, double eps, int max_iters, in
     ++s->fgen;
   }
   s->rho = rho; s->eps = eps; s->max_iters = max_iters; s->accel = accel; s->eta = eta;
+  graph_invalidate(s);
   return PIMPC_OK;
 }
 
@@ -715,12 +805,34 @@ int pimpc_factorise(pimpc_solver *s, void *stream) {
   return PIMPC_OK;
 }
 
+int pimpc_set_graph(pimpc_solver *s, int enable) {
+  if (!s) return PIMPC_EINVAL;
+  if (enable != 0 && enable != 1) return fail(s, PIMPC_EINVAL, "enable must be 0 or 1");
+  cudaSetDevice(s->device);
+  graph_invalidate(s);
+  s->graph_on = enable;
+  s->graph_failed = 0;
+  s->graph_err.clear();
+  return PIMPC_OK;
+}
+
+int pimpc_get_graph_stats(pimpc_solver *s, int *enabled, long long *captures, long long *replays,
+                          const char **refused) {
+  if (!s) return PIMPC_EINVAL;
+  if (enabled) *enabled = s->graph_on && !s->graph_failed;
+  if (captures) *captures = s->graph_captures;
+  if (replays) *replays = s->graph_replays;
+  if (refused) *refused = s->graph_failed ? s->graph_err.c_str() : nullptr;
+  return PIMPC_OK;
+}
+
 int pimpc_set_polish(pimpc_solver *s, int polish_iters, double polish_eps) {
   if (!s) return PIMPC_EINVAL;
   if (polish_iters < 0) return fail(s, PIMPC_EINVAL, "polish_iters < 0");
   if (std::isnan(polish_eps)) return fail(s, PIMPC_EINVAL, "polish_eps is NaN");
   s->polish_iters = polish_iters;
   s->polish_eps = polish_eps;
+  graph_invalidate(s);
   return PIMPC_OK;
 }
 
@@ -741,11 +853,18 @@ int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const d
   double *u_dev = u_out ? (dev ? u_out : s->out_u) : nullptr;
   double *x_dev = x_out ? (dev ? x_out : s->out_x) : nullptr;
   const bool polish = s->polish_iters > 0 && s->prec == PIMPC_F32;
+  if (dev && s->graph_on && !s->graph_failed) {
+    const int rc = graph_solve(s, dx0, dup, dref, ref_per_stage, warm_start, u_dev, x_dev, iters,
+                               c, status, polish, st);
+    if (rc != PIMPC_OK || !s->graph_failed) return rc;
+    // the capture was refused: this call and the later ones run the launches directly
+  }
   int rc = run_solve(s, dx0, dup, dref, ref_per_stage, warm_start, polish ? nullptr : u_dev,
                      polish ? nullptr : x_dev, st);
   if (rc != PIMPC_OK) return rc;
   if (polish) {
-    rc = run_polish(s, dx0, dup, dref, ref_per_stage, u_dev, x_dev, st);
+    rc = prepare_polish(s, st);
+    if (rc == PIMPC_OK) rc = polish_launch(s, dx0, dup, dref, ref_per_stage, u_dev, x_dev, st);
     if (rc != PIMPC_OK) return rc;
   }
   s->last_polished = polish;
@@ -822,6 +941,7 @@ int pimpc_set_restart_mask(pimpc_solver *s, const unsigned char *mask, int len, 
   if (!s) return PIMPC_EINVAL;
   cudaSetDevice(s->device);
   cudaStream_t st = (cudaStream_t)stream;
+  graph_invalidate(s);
   if (!mask) { s->mask_len = 0; s->mask = nullptr; return PIMPC_OK; }
   if (len < 0 || len > s->max_iters) return fail(s, PIMPC_EINVAL, "mask length must be in [0, max_iters]");
   // Testing aid: the mask buffer is (re)allocated here, sized for this mask.

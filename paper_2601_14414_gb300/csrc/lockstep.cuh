@@ -284,7 +284,19 @@ cudaError_t launch_sequence(const AdmmLaunch &s, Args<T> &a, const void *kernel,
   if (s.max_iters > 0) {
     rc = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (rc != cudaSuccess) return rc;
-    rc = cudaLaunchCooperativeKernel(kernel, dim3(s.grid), dim3(s.threads), params, smem, stream);
+    // Cooperative launch (all CTAs co-resident: the grid barrier relies on it), issued through
+    // cudaLaunchKernelExC so that it can also be recorded into a CUDA graph.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(s.grid);
+    cfg.blockDim = dim3(s.threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    rc = cudaLaunchKernelExC(&cfg, kernel, params);
     if (rc != cudaSuccess) return rc;
   }
   output_kernel<T><<<dim3(4, s.L.batch), 256, 0, stream>>>(a, s.u_out, s.x_out);

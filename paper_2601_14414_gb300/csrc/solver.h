@@ -1,5 +1,6 @@
 // solver.h -- the solver object behind the opaque pimpc_solver handle (internal to the library).
 #pragma once
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,18 @@ struct pimpc_solver {
   pimpc_solver *shadow = nullptr;
   long fgen = 0, shadow_fgen = -1;   // generation of the factorisation inputs
   bool last_polished = false;
+  // CUDA graphs of device-memory solves: one per argument set, replayed on later calls; every
+  // call that changes launch parameters drops them
+  struct GraphEntry {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+    int warm, ref_per_stage, ref_given, polished;
+  };
+  int graph_on = 0, graph_failed = 0;
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  long graph_captures = 0, graph_replays = 0;
+  std::string graph_err;
   // adjoint workspace (allocated by the first pimpc_backward)
   void *adj_ws = nullptr;
   size_t adj_ws_bytes = 0;
@@ -59,6 +72,7 @@ struct pimpc_solver {
 
 namespace pimpc {
 int fail(pimpc_solver *s, int code, const std::string &msg);
+void graph_invalidate(pimpc_solver *s);
 int apply_schedule(pimpc_solver *s, const Schedule &sc, std::string &why);
 int cuda_fail(pimpc_solver *s, cudaError_t e, const char *what);
 size_t tsize(int prec);

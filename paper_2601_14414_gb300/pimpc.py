@@ -50,6 +50,8 @@ _SIGS = {
     "pimpc_solve_static": (_I, [_I, _I, _I, _I] + [_VP] * 11 + [_D, _D, _I, _I, _D] + [_VP] * 6),
     "pimpc_set_schedule": (_I, [_VP, _I, _I, _I]),
     "pimpc_set_polish": (_I, [_VP, _I, _D]),
+    "pimpc_set_graph": (_I, [_VP, _I]),
+    "pimpc_get_graph_stats": (_I, [_VP] * 5),
     "pimpc_get_schedule": (_I, [_VP] * 7),
     "pimpc_autotune": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP]),
 }
@@ -233,6 +235,19 @@ def pimpc_solve_static(nx, nu, N, precision, A, B, e, q, r, xmin, xmax, umin, um
 
 
 FAMILY_LANES, FAMILY_TILES = 0, 2
+
+
+def pimpc_set_graph(h, enable):
+    _check(h, load().pimpc_set_graph(h, int(bool(enable))))
+
+
+def pimpc_get_graph_stats(h):
+    en, cap, rep = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+    why = ctypes.c_char_p()
+    _check(h, load().pimpc_get_graph_stats(h, ctypes.byref(en), ctypes.byref(cap),
+                                           ctypes.byref(rep), ctypes.byref(why)))
+    return dict(enabled=bool(en.value), captures=cap.value, replays=rep.value,
+                refused=why.value.decode() if why.value else None)
 
 
 def pimpc_set_polish(h, polish_iters, polish_eps=0.0):

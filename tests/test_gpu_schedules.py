@@ -133,3 +133,73 @@ def test_adjoint_on_halo_tiles():
             ref = fd(inst, Wu[j], Wx[j], 40, name)
             got = np.asarray(g[name][j]).reshape(ref.shape)
             assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, float(np.max(np.abs(ref)))), name
+
+
+# ---- CUDA graphs of device-memory solves ----------------------------------------------------
+
+def device_solve(s, dev_args):
+    x0, up, ref, u, x, it, c, st = dev_args
+    pimpc.pimpc_solve(s.h, x0, up, ref, s.p["ref_per_stage"], 0, u, x, it, c, st)
+
+
+def test_graph_replays_give_the_direct_results():
+    import torch
+    insts = ragged_batch(41)
+    dev = torch.device("cuda")
+    t = lambda a: None if a is None else torch.from_numpy(np.asarray(a, np.float64)).to(dev)
+    eager = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=100, accel=0)
+    graph = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=100, accel=0)
+    pimpc.pimpc_set_graph(graph.h, 1)
+    p = eager.p
+    outs = lambda: (torch.zeros(int(np.sum(eager.N * eager.nu)), dtype=torch.float64, device=dev),
+                    torch.zeros(int(np.sum(eager.N * eager.nx)), dtype=torch.float64, device=dev),
+                    torch.zeros(eager.batch, dtype=torch.int32, device=dev),
+                    torch.zeros(eager.batch, dtype=torch.float64, device=dev),
+                    torch.zeros(eager.batch, dtype=torch.int32, device=dev))
+    ins = (t(p["x0"]), t(p["u_prev"]), t(p["ref"]))
+    a = ins + outs()
+    g = ins + outs()
+    device_solve(eager, a)
+    for rep in range(3):
+        g[3].zero_()
+        device_solve(graph, g)
+        torch.cuda.synchronize()
+        assert torch.equal(a[3], g[3]) and torch.equal(a[4], g[4]) and torch.equal(a[5], g[5])
+    stats = pimpc.pimpc_get_graph_stats(graph.h)
+    assert stats["refused"] is None, stats
+    assert stats["enabled"] and stats["captures"] == 1 and stats["replays"] == 2
+    # new options drop the graph; the next call records a new one
+    graph.set_options(-1.0, 60, 0)
+    eager.set_options(-1.0, 60, 0)
+    device_solve(eager, a)
+    device_solve(graph, g)
+    torch.cuda.synchronize()
+    assert torch.equal(a[3], g[3]) and pimpc.pimpc_get_graph_stats(graph.h)["captures"] == 2
+
+
+def test_graph_with_polish_and_accel():
+    import torch
+    insts = ragged_batch(42, dims=[(4, 2, 37), (14, 2, 19), (24, 8, 45)])
+    dev = torch.device("cuda")
+    t = lambda a: None if a is None else torch.from_numpy(np.asarray(a, np.float64)).to(dev)
+    ref = oracle.solve_batch(insts, eps=1e-22, max_iters=200000, accel=1)
+    s = pimpc.Solver(insts, precision=pimpc.F32, eps=1e-8, max_iters=20000, accel=1)
+    s.set_polish(200000, 1e-22)
+    pimpc.pimpc_set_graph(s.h, 1)
+    p = s.p
+    u = torch.zeros(int(np.sum(s.N * s.nu)), dtype=torch.float64, device=dev)
+    x = torch.zeros(int(np.sum(s.N * s.nx)), dtype=torch.float64, device=dev)
+    st = torch.zeros(s.batch, dtype=torch.int32, device=dev)
+    x0d = t(p["x0"])
+    for rep in range(2):
+        u.zero_()
+        x.zero_()
+        pimpc.pimpc_solve(s.h, x0d, None, None, False, 0, u, x, None, None, st)
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == pimpc.CONVERGED).all()
+        us = pimpc.split(u.cpu().numpy(), s.N * s.nu)
+        xs = pimpc.split(x.cpu().numpy(), s.N * s.nx)
+        for j, o in enumerate(ref):
+            assert solution_error(us[j], xs[j], o["u"], o["x"]) <= 1e-9
+    stats = pimpc.pimpc_get_graph_stats(s.h)
+    assert stats["refused"] is None and stats["captures"] == 1 and stats["replays"] == 1
