@@ -43,6 +43,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=None, help="instances per GPU (default 4096)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the further rows (polish, adjoint, latency, RTI, large state)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling driver: only the FP32 factorise + solve steps, no reference, "
                          "e2e or CPU legs; prints the algorithmic bytes of the solve launch")
@@ -192,6 +194,217 @@ def oracle_sample(insts, cfg, seconds_hint, rng_seed=0):
             break
     dt = time.perf_counter() - t0
     return done, dt, threads
+
+
+# ---------------------------------------------------------------------------------------------
+# Further rows measured on the same GPU (rank 0): each returns a dict, or an error entry.
+# ---------------------------------------------------------------------------------------------
+
+def extra(fn, *a, **kw):
+    try:
+        return fn(*a, **kw)
+    except Exception as ex:  # one failing extra must not lose the benchmark line
+        return dict(error=f"{type(ex).__name__}: {ex}")
+
+
+def accuracy_count(u, x, u_ref, x_ref, ou, ox, tol):
+    err = np.array([np.max(np.abs(np.concatenate([u[ou[j]:ou[j + 1]], x[ox[j]:ox[j + 1]]]) -
+                                  np.concatenate([u_ref[ou[j]:ou[j + 1]], x_ref[ox[j]:ox[j + 1]]])))
+                    / max(1.0, np.max(np.abs(np.concatenate([u_ref[ou[j]:ou[j + 1]],
+                                                             x_ref[ox[j]:ox[j + 1]]]))))
+                    for j in range(len(ou) - 1)])
+    return int(np.sum(err <= tol)), err
+
+
+def bench_polish(torch, pimpc, make, d, p, cfg, tot_u, tot_x, refs, ou, ox):
+    """The headline workload with the FP64 polish: FP32 iterations to eps, then FP64 iterations
+    (FP64 cache) to polish_eps; every step refreshes the dynamics, so both caches are rebuilt."""
+    stream = torch.cuda.current_stream()
+    h = make(pimpc.F32, cfg["eps"], cfg["max_iters"])
+    pimpc.pimpc_set_polish(h, cfg["polish_iters"], cfg["polish_eps"])
+    dev = d["x0"].device
+    u = torch.zeros(tot_u, dtype=torch.float64, device=dev)
+    x = torch.zeros(tot_x, dtype=torch.float64, device=dev)
+
+    def step():
+        pimpc.pimpc_set_dynamics(h, d["A"], d["B"], d["e"])
+        pimpc.pimpc_factorise(h, stream.cuda_stream)
+        pimpc.pimpc_solve(h, d["x0"], None, d["ref"], p["ref_per_stage"], 0, u, x)
+
+    step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    ok, err = accuracy_count(u.cpu().numpy(), x.cpu().numpy(), refs[0], refs[1], ou, ox,
+                             cfg["accuracy"])
+    iters = np.zeros(len(ou) - 1, np.int32)
+    pimpc.pimpc_get_stats(h, iters, None, None, None)
+    pimpc.pimpc_destroy(h)
+    return dict(value=ok / (ms / 1e3), unit="solves/s", ms_per_step=ms, ok=ok, of=len(ou) - 1,
+                median_err=float(np.median(err)), polish_iters=cfg["polish_iters"],
+                polish_eps=cfg["polish_eps"], mean_iters_fp32_plus_fp64=float(np.mean(iters)),
+                steps=1, warmup=1)
+
+
+def bench_cartpole(torch, pimpc, W, steps):
+    """Differentiable MPC: 1024 cart-pole instances (N = 100), 150 plain FP32 iterations,
+    forward solve + reverse sweep with checkpoints every 25 iterations, device memory."""
+    insts = W.cartpole_batch()
+    iters, K = 150, 25
+    s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=iters, accel=0)
+    prm = np.ascontiguousarray(np.concatenate([i["params"] for i in insts]))
+    xb = np.ascontiguousarray(np.concatenate([i["op_x"] for i in insts]))
+    ub = np.ascontiguousarray(np.concatenate([i["op_u"] for i in insts]))
+    pimpc.pimpc_linearise(s.h, W.MODEL_CARTPOLE, prm, insts[0]["dt"], xb, ub)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev)
+    x0, ref = t(s.p["x0"]), t(s.p["ref"])
+    tu, tx = int(np.sum(s.N * s.nu)), int(np.sum(s.N * s.nx))
+    u = torch.zeros(tu, dtype=torch.float64, device=dev)
+    x = torch.zeros(tx, dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(4)
+    gu, gx = t(rng.standard_normal(tu)), t(rng.standard_normal(tx))
+    outs = [torch.zeros(n, dtype=torch.float64, device=dev)
+            for n in (int(np.sum(s.nx)), int(np.sum(s.nx + s.nu)), int(np.sum(s.nx)),
+                      int(np.sum(s.nu)), int(np.sum(s.nx)), int(np.sum(s.nx)),
+                      int(np.sum(s.nu)), int(np.sum(s.nu)))]
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+
+    def bwd():
+        pimpc.pimpc_backward(s.h, gu, gx, *outs, checkpoint_every=K)
+
+    for _ in range(2):
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
+    for k in range(steps):
+        ev[3 * k].record(stream)
+        fwd()
+        ev[3 * k + 1].record(stream)
+        bwd()
+        ev[3 * k + 2].record(stream)
+    torch.cuda.synchronize()
+    f_ms = float(np.mean([ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(steps)]))
+    b_ms = float(np.mean([ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(steps)]))
+    s.close()
+    return dict(value=len(insts) / ((f_ms + b_ms) / 1e3), unit="forward+backward solves/s",
+                forward_ms=f_ms, backward_ms=b_ms, instances=len(insts), N=100, iterations=iters,
+                checkpoint_every=K, dtype="f32", steps=steps, warmup=2)
+
+
+def bench_latency(torch, pimpc, W, reps=50):
+    """One plain LTI instance (nx 4, nu 2, N 20), FP64, 200 iterations: time per solve with
+    direct launches and with the solve replayed from a CUDA graph (device memory)."""
+    inst = W.plain_lti()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    for mode in ("direct", "graph"):
+        s = pimpc.Solver([inst], precision=pimpc.F64, eps=-1.0, max_iters=200, accel=0)
+        if mode == "graph":
+            pimpc.pimpc_set_graph(s.h, 1)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev)
+        x0, ref = t(s.p["x0"]), t(s.p["ref"])
+        u = torch.zeros(40, dtype=torch.float64, device=dev)
+        x = torch.zeros(80, dtype=torch.float64, device=dev)
+        for _ in range(10):
+            pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+        b.record()
+        torch.cuda.synchronize()
+        out[mode + "_us_per_solve"] = 1e3 * a.elapsed_time(b) / reps
+        if mode == "graph":
+            out["graph"] = pimpc.pimpc_get_graph_stats(s.h)
+        s.close()
+    out["us_per_iteration_graph"] = out["graph_us_per_solve"] / 200
+    out.update(workload="plain LTI nx 4, nu 2, N 20, FP64, 200 iterations", reps=reps)
+    return out
+
+
+def bench_rti(torch, pimpc, W, precision, steps=50):
+    """Quadrotor NMPC by real-time iteration (N = 200, 100 iterations per sample, warm start):
+    per sample linearise along the shifted previous solution, factorise, solve, plant step; all
+    on device memory."""
+    wl = W.quadrotor_rti()
+    nx, nu, N = wl["nx"], wl["nu"], wl["N"]
+    inst = {k: wl[k] for k in ("nx", "nu", "N", "q", "r", "rdu", "xmin", "xmax", "umin", "umax",
+                               "u_prev", "rho")}
+    inst.update(lti=False, x0=wl["x0"], ref=W.quadrotor_reference(wl, 0))
+    s = pimpc.Solver([inst], precision=precision, eps=-1.0, max_iters=wl["iters"], accel=1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev)
+    prm = t(wl["params"])
+    refs = [t(W.quadrotor_reference(wl, k)) for k in range(steps)]
+    x = t(wl["x0"])
+    u = torch.zeros(N * nu, dtype=torch.float64, device=dev)
+    xs = torch.zeros(N * nx, dtype=torch.float64, device=dev)
+    xn = torch.zeros(nx, dtype=torch.float64, device=dev)
+    xbar = x.repeat(N)
+    ubar = t(wl["hover_u"]).repeat(N)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(steps):
+        pimpc.pimpc_linearise(s.h, wl["model"], prm, wl["dt"], xbar, ubar)
+        pimpc.pimpc_solve(s.h, x, None, refs[k], False, 1 if k else 0, u, xs)
+        pimpc.pimpc_plant_step(s.h, wl["model"], prm, wl["dt"], x, u[:nu].contiguous(), xn)
+        x.copy_(xn)
+        xbar = torch.cat([x, xs[nx:]])
+        ubar = torch.cat([u[nu:], u[-nu:]])
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    s.close()
+    return dict(value=steps / (ms / 1e3), unit="RTI samples/s", ms_per_sample=ms / steps,
+                us_per_iteration=1e3 * ms / steps / wl["iters"], samples=steps, N=N,
+                iterations_per_sample=wl["iters"],
+                dtype="f64" if precision == pimpc.F64 else "f32",
+                final_position=x[:3].cpu().numpy().tolist())
+
+
+def bench_large_lti(torch, pimpc, W):
+    """256 LTI instances, nx 48, nu 16, N 1000: FP32 and FP64 solves to c <= 1e-10 (primal and
+    dual changes about 1e-5), accelerated; time, iterations and the FP32 vs FP64 difference."""
+    insts = W.large_lti()
+    res = {}
+    outs = {}
+    for name, prec, word in (("f32", pimpc.F32, 4), ("f64", pimpc.F64, 8)):
+        s = pimpc.Solver(insts, precision=prec, eps=1e-10, max_iters=20000, accel=1)
+        s.solve()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.solve()
+        dt = time.perf_counter() - t0
+        iters = np.zeros(len(insts), np.int32)
+        mom = np.zeros(len(insts), np.int32)
+        pimpc.pimpc_get_stats(s.h, iters, None, None, mom)
+        n = 64
+        alg = float(np.sum(1000 * (iters.astype(np.int64) * 10 * n + mom * 5 * n))) * word
+        res[name] = dict(seconds_per_solve=dt, mean_iters=float(np.mean(iters)),
+                         converged=int(np.sum(r["status"] == pimpc.CONVERGED)),
+                         stage_iters_per_s=float(np.sum(iters) * 1000 / dt),
+                         iterate_gb_per_s=alg / dt / 1e9)
+        outs[name] = r
+        s.close()
+    diff = max(float(np.max(np.abs(np.concatenate([a.ravel(), b.ravel()]) -
+                                   np.concatenate([c.ravel(), e.ravel()])))
+                     / max(1.0, np.max(np.abs(np.concatenate([c.ravel(), e.ravel()])))))
+               for a, b, c, e in zip(outs["f32"]["u"], outs["f32"]["x"], outs["f64"]["u"],
+                                     outs["f64"]["x"]))
+    res.update(max_rel_diff_f32_vs_f64=diff, instances=len(insts), N=1000, nx=48, nu=16,
+               note="wall time of a host-memory solve; iterates only: stage matrices are shared")
+    return res
 
 
 def run_reference(args):
@@ -424,6 +637,16 @@ def run_ours(args):
                        sample=f"{n_cpu} random instances of the {batch}-instance workload "
                               f"(all iterations to the same eps), {dt_cpu:.1f} s")
 
+        extras = dict(
+            fp64_polish=extra(bench_polish, torch, pimpc, make, d, p, cfg, tot_u, tot_x, (ur, xr),
+                              ou, ox),
+            differentiable_cartpole=extra(bench_cartpole, torch, pimpc, W, args.steps),
+            single_instance_latency=extra(bench_latency, torch, pimpc, W),
+            quadrotor_rti_f64=extra(bench_rti, torch, pimpc, W, pimpc.F64),
+            quadrotor_rti_f32=extra(bench_rti, torch, pimpc, W, pimpc.F32),
+            large_state_lti=extra(bench_large_lti, torch, pimpc, W),
+        ) if not args.no_extras else None
+
         n_stages = int(np.sum(N))
         stage_bytes = float(np.sum(N * (matrix_words(nx, nu) + 10 * (nx + nu)))) * 4
         line = dict(
@@ -449,8 +672,9 @@ def run_ours(args):
             fp64_single_instance_gpu=single,
             cpu_baseline=cpu,
             e2e=e2e,
-            gpu_launches=4 * args.steps,
+            gpu_launches=8 * args.steps,
             clocks=clk,
+            extras=extras,
         )
         print(json.dumps(line), flush=True)
     pimpc.pimpc_destroy(h)

@@ -14,6 +14,8 @@ BATCHED_UNEVEN = dict(
     accuracy=1e-4,     # a solve counts when max|w - w*| / max(1, max|w*|) <= accuracy
     ref_eps=1e-15,     # FP64 reference solve (same GPU) used to score accuracy
     ref_max_iters=40000,
+    polish_iters=2000,  # FP64 polish variant: FP64 iterations after the FP32 ones ...
+    polish_eps=1e-13,   # ... until c <= polish_eps
 )
 
 # Plain single-instance linear MPC (nx=4, nu=2, N=20), 200 iterations.
