@@ -108,16 +108,20 @@ def batched_dims(seed=3, batch=4096, nx_range=(4, 24), nu_range=(2, 8), N_range=
     return nxs, nus, Ns
 
 
-def large_lti(seed=5, batch=256, nx=48, nu=16, N=1000, radius=0.95, umax=None, rho=1.0):
-    """Large-state LTI stress workload: Q = diag U[0.1, 10], R = diag U[0.01, 1], |x| <= 5 and an
-    input bound chosen so that roughly a fifth of the stages have an active input bound."""
+def large_lti(seed=5, batch=256, nx=48, nu=16, N=1000, radius=0.95, umax=None, rho=1.0,
+              e_scale=0.3):
+    """Large-state LTI stress workload: Q = diag U[0.1, 10], R = diag U[0.01, 1], a constant
+    disturbance e ~ U[-0.3, 0.3] (the paper's random-system recipe; it keeps the inputs busy over
+    the whole horizon), |x| <= 5 and an input bound chosen so that roughly a fifth of the input
+    values would exceed it without the bound."""
     rng = np.random.default_rng(seed)
     umax = LARGE_LTI_UMAX if umax is None else umax
     out = []
     for _ in range(batch):
         A = _scaled_gaussian(rng, nx, radius)
         B = rng.standard_normal((nx, nu))
-        inst = dict(nx=nx, nu=nu, N=N, lti=True, A=A, B=B, e=np.zeros(nx),
+        e = rng.uniform(-e_scale, e_scale, nx)
+        inst = dict(nx=nx, nu=nu, N=N, lti=True, A=A, B=B, e=e,
                     q=rng.uniform(0.1, 10.0, nx), r=rng.uniform(0.01, 1.0, nu), rdu=None,
                     x0=rng.uniform(-3, 3, nx), u_prev=None, ref=np.zeros(nx + nu), rho=rho)
         inst.update(_box(nx, nu, 5.0, umax))
