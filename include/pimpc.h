@@ -257,11 +257,14 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
  * up to the order of the sums in c).
  *   family       0: a group of lanes per stage on plain stage blocks (every precision and
  *                   instance kind; the default); 2: one thread per stage on halo tiles
- *                   (stage-varying FP32 instances only); -1: the default.
+ *                   (stage-varying FP32 instances only); 3: every instance resident in the
+ *                   shared memory of one CTA or of a thread-block cluster for the whole solve
+ *                   (no grid-wide synchronisation; for instances that fit); -1: the default.
  *   ctas_per_sm  family 2: CTAs per SM the shared-memory budget of a CTA is sized for
- *                (0 = 2); ignored by family 0.
+ *                (0 = 2); ignored by families 0 and 3.
  *   item_scale   family 0: stage sub-chunks per work item (0 = automatic); family 2: at most
- *                this many tiles per work item (0 = 4).
+ *                this many tiles per work item (0 = 4); family 3: CTAs per instance, 1, 2, 4,
+ *                8 or 16 (0 = the fewest whose shared memory holds the instance).
  * pimpc_set_schedule re-lays out the stage data and the iterates: the next solve factorises
  * again and starts cold (warm_start is treated as 0 until one solve has run).
  * Errors: PIMPC_EINVAL (a bad value, or an instance that does not fit the schedule; the
@@ -281,7 +284,8 @@ int pimpc_get_schedule(pimpc_solver *s, int *family, int *ctas_per_sm, int *item
  * pimpc_autotune -- times trial_iters iterations (zero start, no reference, the accel option in
  * force) of every candidate schedule on this solver's batch, with its current dynamics, weights
  * and bounds, using CUDA events on `stream`, and keeps the fastest. Candidates: family 0 with
- * item_scale 0, 2 and 8; family 2 with 1 and 2 CTAs per SM where the batch allows it. The
+ * item_scale 0, 2 and 8; family 3 where the instances fit; family 2 with 1 and 2 CTAs per SM
+ * where the batch allows it. The
  * chosen schedule and its time (ms, the second of two trial solves) are returned through the
  * pointers (host memory, any may be NULL). The stage cache and the iterates are rebuilt as for
  * pimpc_set_schedule. Blocks the host until the trials finish.

@@ -116,7 +116,10 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   const size_t ts = tsize(precision);
   const std::vector<int> &nx = s->nx, &nu = s->nu, &N = s->N;
   if (sc.family < 0) sc.family = 0;  // lane groups; halo tiles are chosen explicitly or by the autotuner
-  if (sc.family != 0 && sc.family != 2) { why = "schedule family must be 0 or 2"; return PIMPC_EINVAL; }
+  if (sc.family != 0 && sc.family != 2 && sc.family != 3) {
+    why = "schedule family must be 0, 2 or 3";
+    return PIMPC_EINVAL;
+  }
   if (sc.family == 2 && (precision != PIMPC_F32 || lti)) {
     why = "halo tiles serve stage-varying FP32 instances";
     return PIMPC_EINVAL;
@@ -125,7 +128,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     why = "schedule: ctas_per_sm in 0..8, item_scale in 0..64";
     return PIMPC_EINVAL;
   }
-  const int tiled = sc.family;
+  const int tiled = sc.family == 2 ? 2 : 0;  // the resident family uses the plain layout
   s->tiled = tiled;
   int nsm = 0, smem_sm = 0, optin = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
@@ -235,6 +238,30 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
       return PIMPC_EINVAL;
     }
     e = admm_configure(precision, s->smem_admm, &bps);
+    if (sc.family == 3 && e == cudaSuccess) {
+      // One CTA or a cluster per instance: the fewest CTAs whose shared memory holds a slice.
+      const int thr = res_threads(precision);
+      int plan[6];
+      size_t bytes = 0;
+      int C = 0;
+      for (int cand : {1, 2, 4, 8, 16}) {
+        if (sc.item_scale > 0 && cand != sc.item_scale) continue;
+        const size_t b = res_plan(batch, nx.data(), nu.data(), N.data(), W.data(), lti, precision,
+                                  thr, cand, plan);
+        if (b > 0 && b + 1024 <= (size_t)optin - 256) {
+          bytes = b;
+          C = cand;
+          break;
+        }
+      }
+      if (C == 0) {
+        why = "the instances do not fit the shared memory of a cluster of that size (or N < cluster size)";
+        return PIMPC_EINVAL;
+      }
+      std::copy(plan, plan + 6, s->res_plan);
+      P.threads = thr;
+      s->smem_admm = bytes;
+    }
     if (e == cudaSuccess && bps >= 1) {
       const int64_t max_grid = (int64_t)bps * nsm;
       // Sub-chunks per item: enough items for about 4 per CTA, at most 16 sub-chunks per item.
@@ -360,7 +387,10 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.warm = warm_start;
   a.u_out = u_dev;
   a.x_out = x_dev;
-  PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st) : launch_admm(a, s->prec, st), "solve");
+  PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st)
+                 : s->sched.family == 3 ? launch_resident(a, s->prec, s->res_plan, s->smem_admm, st)
+                                        : launch_admm(a, s->prec, st),
+              "solve");
   s->solved = true;
   s->last_ref_per_stage = ref_per_stage;
   s->last_ref_given = dref != nullptr;

@@ -52,10 +52,19 @@ int tile_warps();
 cudaError_t tile_configure(size_t smem, int *blocks_per_sm);
 cudaError_t launch_tile(const AdmmLaunch &a, cudaStream_t stream);
 
+// Every instance resident on chip: one CTA or a cluster of C CTAs per instance.
+int res_threads(int precision);
+size_t res_plan(int batch, const int *nx, const int *nu, const int *N, const int *W, int lti,
+                int precision, int threads, int C, int *plan);
+cudaError_t launch_resident(const AdmmLaunch &s, int precision, const int *plan, size_t smem,
+                            cudaStream_t stream);
+
 // Schedule of the batched solve: which kernel family and how its work is cut.
 struct Schedule {
   int family = -1;       // 0: lane groups on plain stage blocks; 2: one thread per stage on halo
-                         // tiles (stage-varying FP32 only); -1: the default for the batch
+                         // tiles (stage-varying FP32 only); 3: every instance resident in the
+                         // shared memory of one CTA or a cluster (item_scale = CTAs per
+                         // instance, 0: the fewest that fit); -1: the default for the batch
   int ctas_per_sm = 0;   // halo tiles: CTAs per SM the shared-memory budget is sized for (0: 2)
   int item_scale = 0;    // lane groups: sub-chunks per item (0: automatic);
                          // halo tiles: at most this many tiles per item (0: 4)

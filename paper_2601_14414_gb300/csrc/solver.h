@@ -10,6 +10,7 @@ struct pimpc_solver {
   int device = 0, batch = 0, lti = 0, prec = 0, tiled = 1;
   std::vector<int> nx, nu, N, W, tw;
   pimpc::Schedule sched{};
+  int res_plan[6] = {0, 0, 0, 0, 0, 0};   // resident schedule: cluster size and smem regions
   std::vector<void *> lay_allocs;   // buffers whose size depends on the schedule
   std::vector<int64_t> off_nx, off_nu, off_n, Nnx, Nnu, Nn, Ni, offA, offB, offe, blk, stage0, bbase;
   int64_t tot_nx = 0, tot_nu = 0, tot_n = 0, tot_Nnx = 0, tot_Nnu = 0, tot_Nn = 0, tot_Ni = 0;

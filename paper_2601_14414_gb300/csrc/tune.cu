@@ -62,6 +62,11 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
     c.item_scale = m;
     cands.push_back(c);
   }
+  {
+    Schedule c;
+    c.family = 3;  // resident: skipped below when the instances do not fit
+    cands.push_back(c);
+  }
   if (s->prec == PIMPC_F32 && !s->lti)
     for (int cps : {1, 2}) {
       Schedule c;

@@ -203,3 +203,130 @@ def test_graph_with_polish_and_accel():
             assert solution_error(us[j], xs[j], o["u"], o["x"]) <= 1e-9
     stats = pimpc.pimpc_get_graph_stats(s.h)
     assert stats["refused"] is None and stats["captures"] == 1 and stats["replays"] == 1
+
+
+# ---- every instance resident on chip (one CTA or a cluster per instance) -------------------
+
+SMALL_DIMS = [(4, 2, 20), (3, 1, 1), (6, 2, 9), (12, 4, 33), (5, 3, 17), (9, 9, 12)]
+
+
+def resident_solver(insts, precision, cluster=0, **kw):
+    s = pimpc.Solver(insts, precision=precision, **kw)
+    s.set_schedule(pimpc.FAMILY_RESIDENT, 0, cluster)
+    assert s.schedule()["family"] == pimpc.FAMILY_RESIDENT
+    return s
+
+
+@pytest.mark.parametrize("accel", [0, 1])
+def test_resident_fp64_matches_oracle(accel):
+    insts = ragged_batch(51, dims=SMALL_DIMS)
+    s = resident_solver(insts, pimpc.F64, eps=-1.0, max_iters=200, accel=accel)
+    res = s.solve()
+    its = s.iterates()
+    ora = oracle.solve_batch(insts, eps=-1.0, max_iters=200, accel=accel)
+    for j, o in enumerate(ora):
+        for key in ("z", "v", "th", "be", "la"):
+            assert relerr(its[j][key], o[key]) <= 1e-10, (j, key)
+        assert relerr(res["u"][j], o["u"]) <= 1e-10
+        assert res["iters"][j] == 200 and res["status"][j] == pimpc.MAXITER
+        assert abs(res["c"][j] - o["c"]) <= 1e-8 * o["c"] + 1e-24
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8, 16])
+def test_resident_clusters_match_oracle(cluster):
+    """Instances split over clusters of 2..16 CTAs: the boundary stages cross CTAs through
+    distributed shared memory (N not a multiple of the cluster size)."""
+    insts = ragged_batch(52 + cluster, dims=[(12, 4, 61), (4, 2, 37), (24, 8, 19), (7, 3, 16)])
+    s = resident_solver(insts, pimpc.F64, cluster, eps=-1.0, max_iters=150, accel=1)
+    res = s.solve()
+    ora = oracle.solve_batch(insts, eps=-1.0, max_iters=150, accel=1)
+    for j, o in enumerate(ora):
+        assert relerr(res["u"][j], o["u"]) <= 1e-10, j
+        assert relerr(res["x"][j], o["x"]) <= 1e-10, j
+
+
+def test_resident_fp32_and_converged():
+    insts = ragged_batch(53, dims=SMALL_DIMS)
+    K = 200
+    ora = [oracle.solve(i, eps=-1.0, max_iters=K, accel=1, history=True) for i in insts]
+    mask = np.ascontiguousarray(np.stack([o["mask"] for o in ora]).astype(np.uint8))
+    s = resident_solver(insts, pimpc.F32, eps=-1.0, max_iters=K, accel=1)
+    pimpc.pimpc_set_restart_mask(s.h, mask, K)
+    res = s.solve()
+    for j, o in enumerate(ora):
+        assert relerr(res["u"][j], o["u"]) <= 1e-4, j
+        assert relerr(res["x"][j], o["x"]) <= 1e-4, j
+    conv = ragged_batch(4, dims=[(4, 2, 37), (14, 2, 19), (12, 4, 33), (6, 2, 1), (9, 9, 17)])
+    c = resident_solver(conv, pimpc.F32, eps=1e-11, max_iters=20000, accel=1)
+    r = c.solve()
+    oc = oracle.solve_batch(conv, eps=1e-22, max_iters=200000, accel=1)
+    for j, o in enumerate(oc):
+        assert solution_error(r["u"][j], r["x"][j], o["u"], o["x"]) <= 1e-5, j
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_resident_warm_start(mode):
+    insts = ragged_batch(54, dims=[(4, 2, 37), (12, 4, 33)])
+    s = resident_solver(insts, pimpc.F64, 2, eps=-1.0, max_iters=60, accel=1)
+    s.solve()
+    first = s.iterates()
+    s.solve(warm_start=mode)
+    its = s.iterates()
+    for j, inst in enumerate(insts):
+        warm = {k: first[j][k].copy() for k in ("z", "v", "th", "be", "la")}
+        if mode == 2:
+            for k in warm:
+                warm[k] = np.concatenate([warm[k][1:], warm[k][-1:]], axis=0)
+        o = oracle.solve(inst, eps=-1.0, max_iters=60, accel=1, warm=warm)
+        for key in ("z", "v", "th", "be", "la"):
+            assert relerr(its[j][key], o[key]) <= 1e-10, (j, key)
+
+
+def test_resident_stage_invariant_n64():
+    insts = [W.plain_lti(seed=61 + i, nx=48, nu=16, N=40) for i in range(2)]
+    s = resident_solver(insts, pimpc.F64, eps=-1.0, max_iters=80, accel=1)
+    res = s.solve()
+    for j, inst in enumerate(insts):
+        o = oracle.solve(inst, eps=-1.0, max_iters=80, accel=1)
+        assert relerr(res["u"][j], o["u"]) <= 1e-10
+
+
+def test_resident_rejects_what_does_not_fit():
+    insts = ragged_batch(55, dims=[(4, 2, 3)])
+    s = pimpc.Solver(insts, precision=pimpc.F64, eps=-1.0, max_iters=10, accel=0)
+    with pytest.raises(pimpc.PimpcError) as e:
+        s.set_schedule(pimpc.FAMILY_RESIDENT, 0, 4)   # N = 3 < 4 CTAs
+    assert e.value.code == pimpc.EINVAL
+    big = [W.random_ltv(56, 24, 8, 3000)]
+    s2 = pimpc.Solver(big, precision=pimpc.F64, eps=-1.0, max_iters=10, accel=0)
+    with pytest.raises(pimpc.PimpcError):
+        s2.set_schedule(pimpc.FAMILY_RESIDENT, 0, 1)  # far more than one CTA's shared memory
+
+
+def test_resident_graph_and_adjoint():
+    import torch
+    from test_gpu_adjoint import NAMES, fd, loss_weights, small_batch
+    insts = small_batch()
+    Wu, Wx = loss_weights(insts, seed=5)
+    s = resident_solver(insts, pimpc.F64, eps=-1.0, max_iters=40, accel=0)
+    s.solve()
+    g = s.backward(Wu, Wx, checkpoint_every=7)
+    for j, inst in enumerate(insts):
+        for name in NAMES:
+            ref = fd(inst, Wu[j], Wx[j], 40, name)
+            got = np.asarray(g[name][j]).reshape(ref.shape)
+            assert np.max(np.abs(got - ref)) <= 1e-6 * max(1.0, float(np.max(np.abs(ref)))), name
+    # cluster launches recorded into a CUDA graph
+    pimpc.pimpc_set_graph(s.h, 1)
+    dev = torch.device("cuda")
+    x0 = torch.from_numpy(s.p["x0"]).to(dev)
+    up = torch.from_numpy(s.p["u_prev"]).to(dev)
+    ref = torch.from_numpy(s.p["ref"]).to(dev)
+    u = torch.zeros(int(np.sum(s.N * s.nu)), dtype=torch.float64, device=dev)
+    base = s.solve()
+    for _ in range(2):
+        pimpc.pimpc_solve(s.h, x0, up, ref, s.p["ref_per_stage"], 0, u, None)
+    torch.cuda.synchronize()
+    st = pimpc.pimpc_get_graph_stats(s.h)
+    assert st["refused"] is None and st["captures"] == 1 and st["replays"] == 1, st
+    assert np.array_equal(u.cpu().numpy(), np.concatenate([v.ravel() for v in base["u"]]))
