@@ -306,9 +306,11 @@ def bench_latency(torch, pimpc, W, reps=50):
     inst = W.plain_lti()
     dev = torch.device("cuda", torch.cuda.current_device())
     out = {}
-    for mode in ("direct", "graph"):
+    for mode in ("direct", "graph", "resident", "resident_graph"):
         s = pimpc.Solver([inst], precision=pimpc.F64, eps=-1.0, max_iters=200, accel=0)
-        if mode == "graph":
+        if mode.startswith("resident"):
+            s.set_schedule(pimpc.FAMILY_RESIDENT)
+        if mode.endswith("graph"):
             pimpc.pimpc_set_graph(s.h, 1)
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev)
         x0, ref = t(s.p["x0"]), t(s.p["ref"])
@@ -324,24 +326,26 @@ def bench_latency(torch, pimpc, W, reps=50):
         b.record()
         torch.cuda.synchronize()
         out[mode + "_us_per_solve"] = 1e3 * a.elapsed_time(b) / reps
-        if mode == "graph":
-            out["graph"] = pimpc.pimpc_get_graph_stats(s.h)
+        if mode.endswith("graph"):
+            out[mode + "_stats"] = pimpc.pimpc_get_graph_stats(s.h)
         s.close()
-    out["us_per_iteration_graph"] = out["graph_us_per_solve"] / 200
+    out["us_per_iteration_resident_graph"] = out["resident_graph_us_per_solve"] / 200
     out.update(workload="plain LTI nx 4, nu 2, N 20, FP64, 200 iterations", reps=reps)
     return out
 
 
-def bench_rti(torch, pimpc, W, precision, steps=50):
+def bench_rti(torch, pimpc, W, precision, steps=50, family=None):
     """Quadrotor NMPC by real-time iteration (N = 200, 100 iterations per sample, warm start):
     per sample linearise along the shifted previous solution, factorise, solve, plant step; all
-    on device memory."""
+    on device memory. ``family``: the solve's schedule (None: the default)."""
     wl = W.quadrotor_rti()
     nx, nu, N = wl["nx"], wl["nu"], wl["N"]
     inst = {k: wl[k] for k in ("nx", "nu", "N", "q", "r", "rdu", "xmin", "xmax", "umin", "umax",
                                "u_prev", "rho")}
     inst.update(lti=False, x0=wl["x0"], ref=W.quadrotor_reference(wl, 0))
     s = pimpc.Solver([inst], precision=precision, eps=-1.0, max_iters=wl["iters"], accel=1)
+    if family is not None:
+        s.set_schedule(family)
     dev = torch.device("cuda", torch.cuda.current_device())
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev)
     prm = t(wl["params"])
@@ -365,11 +369,13 @@ def bench_rti(torch, pimpc, W, precision, steps=50):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
+    sched = s.schedule()
     s.close()
     return dict(value=steps / (ms / 1e3), unit="RTI samples/s", ms_per_sample=ms / steps,
                 us_per_iteration=1e3 * ms / steps / wl["iters"], samples=steps, N=N,
                 iterations_per_sample=wl["iters"],
                 dtype="f64" if precision == pimpc.F64 else "f32",
+                schedule=dict(family=sched["family"], item_scale=sched["item_scale"]),
                 final_position=x[:3].cpu().numpy().tolist())
 
 
@@ -644,6 +650,10 @@ def run_ours(args):
             single_instance_latency=extra(bench_latency, torch, pimpc, W),
             quadrotor_rti_f64=extra(bench_rti, torch, pimpc, W, pimpc.F64),
             quadrotor_rti_f32=extra(bench_rti, torch, pimpc, W, pimpc.F32),
+            quadrotor_rti_f64_resident=extra(bench_rti, torch, pimpc, W, pimpc.F64,
+                                             family=pimpc.FAMILY_RESIDENT),
+            quadrotor_rti_f32_resident=extra(bench_rti, torch, pimpc, W, pimpc.F32,
+                                             family=pimpc.FAMILY_RESIDENT),
             large_state_lti=extra(bench_large_lti, torch, pimpc, W),
         ) if not args.no_extras else None
 

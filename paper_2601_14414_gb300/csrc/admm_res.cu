@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(256) resident_kernel(Args<T> a, ResPlan pl) {
     if (r == 0)
       for (int c = tid; c < n; c += nthreads) X[c] = a.xb0[a.L.off_n[j] + c];
   }
-  double alpha = 1.0, cprev = 1.0, coef = 0.0;
+  double cprev = 1.0, coef = 0.0;
+  int streak = 0;  // consecutive momentum steps since the last restart
   int momentum = 0, status = kMaxIter, iters = 0;
   double cval = 0.0;
   int cur = 0, prv = 2, nw = 1;
@@ -239,9 +240,16 @@ __global__ void __launch_bounds__(256) resident_kernel(Args<T> a, ResPlan pl) {
     cl.sync();
 
     // ---- steps 4-7, taken identically by every CTA of the cluster ----
+    // Lane q of warp 0 reads the share of CTA q (one round of remote loads); the shares are
+    // added by a fixed butterfly, so lane 0 holds the same sum in every CTA.
+    if (tid < 32) {
+      double s = tid < C ? *cl.map_shared_rank(&sPart, tid) : 0.0;
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (tid == 0) sRed[0] = s;
+    }
+    __syncwarp();
     if (tid == 0) {
-      double s = 0.0;
-      for (int q = 0; q < C; ++q) s += *cl.map_shared_rank(&sPart, q);
+      const double s = sRed[0];
       const double c = a.rho * s;
       cval = c;
       iters = it + 1;
@@ -258,13 +266,12 @@ __global__ void __launch_bounds__(256) resident_kernel(Args<T> a, ResPlan pl) {
           if (a.mask && it < a.mask_len) take = a.mask[(int64_t)j * a.mask_len + it] != 0;
           else take = c <= a.eta * cprev;
         }
-        if (take) {
-          const double an = 0.5 + 0.5 * sqrt(1.0 + 4.0 * alpha * alpha);
-          coef = (alpha - 1.0) / an;
-          if (alpha != 1.0) momentum += 1;
-          alpha = an;
+        if (take) {  // (alpha_m - 1) / alpha_{m+1}, alpha_0 = 1, from the precomputed table
+          coef = a.coef_tab[streak];
+          if (streak > 0) momentum += 1;
+          ++streak;
         } else {
-          alpha = 1.0;
+          streak = 0;
           coef = 0.0;
         }
         cprev = c;
@@ -340,7 +347,23 @@ cudaError_t launch_t(const AdmmLaunch &s, const ResPlan &pl, size_t smem, cudaSt
   return cudaGetLastError();
 }
 
+// tab[m] = (alpha_m - 1) / alpha_{m+1} with alpha_0 = 1, alpha_{m+1} = (1 + sqrt(1 + 4 alpha_m^2))
+// / 2: the momentum factor of Algorithm 1 step 6 after m consecutive momentum steps.
+__global__ void coef_table_kernel(double *tab, int len) {
+  double al = 1.0;
+  for (int m = 0; m < len; ++m) {
+    const double an = 0.5 + 0.5 * sqrt(1.0 + 4.0 * al * al);
+    tab[m] = (al - 1.0) / an;
+    al = an;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_coef_table(double *tab, int len, cudaStream_t stream) {
+  coef_table_kernel<<<1, 1, 0, stream>>>(tab, len);
+  return cudaGetLastError();
+}
 
 int res_threads(int precision) { return precision == 0 ? 256 : 128; }
 

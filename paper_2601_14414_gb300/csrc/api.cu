@@ -38,6 +38,21 @@ int fail(pimpc_solver *s, int code, const std::string &msg) {
   return code;
 }
 
+// The resident kernel's table of momentum factors, long enough for max_iters iterations
+// (computed on the device once per growth; not inside a stream capture).
+int ensure_coef_table(pimpc_solver *s) {
+  if (s->sched.family != 3 || s->coef_len >= s->max_iters + 1) return PIMPC_OK;
+  const int len = std::max(s->max_iters + 1, 1024);
+  if (s->coef_tab) cudaFree(s->coef_tab);
+  s->coef_tab = nullptr;
+  s->coef_len = 0;
+  PIMPC_CHECK(s, cudaMalloc(&s->coef_tab, sizeof(double) * len), "momentum table");
+  PIMPC_CHECK(s, launch_coef_table(s->coef_tab, len, 0), "momentum table");
+  PIMPC_CHECK(s, cudaDeviceSynchronize(), "momentum table");
+  s->coef_len = len;
+  return PIMPC_OK;
+}
+
 void graph_invalidate(pimpc_solver *s) {
   for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
   s->graphs.clear();
@@ -244,15 +259,27 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
       int plan[6];
       size_t bytes = 0;
       int C = 0;
+      // With item_scale = 0: the fewest CTAs that fit, or, when the whole batch occupies few
+      // SMs (latency, not throughput, is what a small batch needs), the most CTAs (up to 16)
+      // that still give every CTA four stages or more.
+      const int nmin = *std::min_element(N.begin(), N.end());
+      int fewest = 0, most = 0;
+      size_t b_few = 0, b_most = 0;
+      int p_few[6], p_most[6];
       for (int cand : {1, 2, 4, 8, 16}) {
         if (sc.item_scale > 0 && cand != sc.item_scale) continue;
         const size_t b = res_plan(batch, nx.data(), nu.data(), N.data(), W.data(), lti, precision,
                                   thr, cand, plan);
-        if (b > 0 && b + 1024 <= (size_t)optin - 256) {
-          bytes = b;
-          C = cand;
-          break;
+        if (b == 0 || b + 1024 > (size_t)optin - 256) continue;
+        if (fewest == 0) { fewest = cand; b_few = b; std::copy(plan, plan + 6, p_few); }
+        if (sc.item_scale > 0 || (nmin >= 4 * cand && (int64_t)batch * cand <= nsm)) {
+          most = cand; b_most = b; std::copy(plan, plan + 6, p_most);
         }
+      }
+      if (most > 0 && most >= fewest) {
+        C = most; bytes = b_most; std::copy(p_most, p_most + 6, plan);
+      } else if (fewest > 0) {
+        C = fewest; bytes = b_few; std::copy(p_few, p_few + 6, plan);
       }
       if (C == 0) {
         why = "the instances do not fit the shared memory of a cluster of that size (or N < cluster size)";
@@ -351,7 +378,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   s->L.W = d_W;
   s->stale = true;
   s->solved = false;
-  return PIMPC_OK;
+  return ensure_coef_table(s);
 }
 
 }  // namespace pimpc
@@ -387,6 +414,9 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.warm = warm_start;
   a.u_out = u_dev;
   a.x_out = x_dev;
+  a.coef_tab = s->coef_tab;
+  if (s->sched.family == 3 && s->coef_len < s->max_iters + 1)
+    return fail(s, PIMPC_ESTATE, "momentum table shorter than max_iters");
   PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st)
                  : s->sched.family == 3 ? launch_resident(a, s->prec, s->res_plan, s->smem_admm, st)
                                         : launch_admm(a, s->prec, st),
@@ -540,6 +570,7 @@ void pimpc_destroy(pimpc_solver *s) {
   for (void *p : s->lay_allocs) cudaFree(p);
   if (s->adj_ws) cudaFree(s->adj_ws);
   if (s->shadow) pimpc_destroy(s->shadow);
+  if (s->coef_tab) cudaFree(s->coef_tab);
   graph_invalidate(s);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->mask_alloc) cudaFree(s->mask_alloc);
@@ -711,6 +742,7 @@ int pimpc_set_options(pimpc_solver *s, double rho, double eps, int max_iters, in
   }
   s->rho = rho; s->eps = eps; s->max_iters = max_iters; s->accel = accel; s->eta = eta;
   graph_invalidate(s);
+  if (const int rc = ensure_coef_table(s)) return rc;
   return PIMPC_OK;
 }
 

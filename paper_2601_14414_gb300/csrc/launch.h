@@ -32,6 +32,7 @@ struct AdmmLaunch {
   double *alpha, *cprev, *coef, *cacc;
   int *ndone, *stop;
   double *u_out, *x_out;
+  const double *coef_tab;
   int warm;
   // launch shape and shared-memory plan (elements of the iteration type)
   int grid, threads;
@@ -54,6 +55,7 @@ cudaError_t launch_tile(const AdmmLaunch &a, cudaStream_t stream);
 
 // Every instance resident on chip: one CTA or a cluster of C CTAs per instance.
 int res_threads(int precision);
+cudaError_t launch_coef_table(double *tab, int len, cudaStream_t stream);
 size_t res_plan(int batch, const int *nx, const int *nu, const int *N, const int *W, int lti,
                 int precision, int threads, int C, int *plan);
 cudaError_t launch_resident(const AdmmLaunch &s, int precision, const int *plan, size_t smem,

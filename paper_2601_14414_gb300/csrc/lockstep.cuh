@@ -37,6 +37,7 @@ struct Args {
   double *alpha, *cprev, *coef, *cacc;
   int *ndone, *stop;
   int capI;
+  const double *coef_tab;  // momentum factor of the m-th consecutive momentum step (resident)
 };
 
 // Iterate element (vector b in {z, v, theta, beta, lambda}, component c) of stage k (its own
@@ -260,6 +261,7 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.alpha = s.alpha; a.cprev = s.cprev; a.coef = s.coef; a.cacc = s.cacc;
   a.ndone = s.ndone; a.stop = s.stop;
   a.capI = 0;
+  a.coef_tab = s.coef_tab;
   return a;
 }
 

@@ -11,6 +11,8 @@ struct pimpc_solver {
   std::vector<int> nx, nu, N, W, tw;
   pimpc::Schedule sched{};
   int res_plan[6] = {0, 0, 0, 0, 0, 0};   // resident schedule: cluster size and smem regions
+  double *coef_tab = nullptr;             // momentum factors by streak length (resident)
+  int coef_len = 0;
   std::vector<void *> lay_allocs;   // buffers whose size depends on the schedule
   std::vector<int64_t> off_nx, off_nu, off_n, Nnx, Nnu, Nn, Ni, offA, offB, offe, blk, stage0, bbase;
   int64_t tot_nx = 0, tot_nu = 0, tot_n = 0, tot_Nnx = 0, tot_Nnu = 0, tot_Nn = 0, tot_Ni = 0;
@@ -73,6 +75,7 @@ struct pimpc_solver {
 
 namespace pimpc {
 int fail(pimpc_solver *s, int code, const std::string &msg);
+int ensure_coef_table(pimpc_solver *s);
 void graph_invalidate(pimpc_solver *s);
 int apply_schedule(pimpc_solver *s, const Schedule &sc, std::string &why);
 int cuda_fail(pimpc_solver *s, cudaError_t e, const char *what);
