@@ -129,9 +129,9 @@ def large_lti(seed=5, batch=256, nx=48, nu=16, N=1000, radius=0.95, umax=None, r
     return out
 
 
-# Input bound of the large-state workload; tests/golden/calibrate_large_lti.py recomputes it with
-# the oracle (80th percentile of |u| of the input-unconstrained solutions).
-LARGE_LTI_UMAX = 1.0
+# Input bound of the large-state workload: the 80th percentile of |u| over the input-unconstrained
+# oracle solutions of the first two instances (tests/golden/calibrate_large_lti.py prints it).
+LARGE_LTI_UMAX = 0.0871132
 
 
 def cartpole_batch(seed=4, batch=1024, N=100, dt=0.05, umax=10.0, rho=1.0):
