@@ -259,12 +259,16 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
  *                   instance kind; the default); 2: one thread per stage on halo tiles
  *                   (stage-varying FP32 instances only); 3: every instance resident in the
  *                   shared memory of one CTA or of a thread-block cluster for the whole solve
- *                   (no grid-wide synchronisation; for instances that fit); -1: the default.
- *   ctas_per_sm  family 2: CTAs per SM the shared-memory budget of a CTA is sized for
- *                (0 = 2); ignored by families 0 and 3.
+ *                   (no grid-wide synchronisation; for instances that fit); 4: stage-invariant
+ *                   instances only, the per-stage products of blocks of stages as dense
+ *                   matrix-matrix contractions; -1: the default.
+ *   ctas_per_sm  families 2 and 4: CTAs per SM the shared-memory budget of a CTA is sized
+ *                for (0 = 2 for family 2, 1 for family 4); ignored by families 0 and 3.
  *   item_scale   family 0: stage sub-chunks per work item (0 = automatic); family 2: at most
  *                this many tiles per work item (0 = 4); family 3: CTAs per instance, 1, 2, 4,
- *                8 or 16 (0 = the fewest whose shared memory holds the instance).
+ *                8 or 16 (0 = the fewest whose shared memory holds the instance, or the most
+ *                that leave each CTA four stages when the batch occupies few SMs); family 4:
+ *                stages per block (0 = as many as the shared memory holds, at most 128).
  * pimpc_set_schedule re-lays out the stage data and the iterates: the next solve factorises
  * again and starts cold (warm_start is treated as 0 until one solve has run).
  * Errors: PIMPC_EINVAL (a bad value, or an instance that does not fit the schedule; the
@@ -284,8 +288,8 @@ int pimpc_get_schedule(pimpc_solver *s, int *family, int *ctas_per_sm, int *item
  * pimpc_autotune -- times trial_iters iterations (zero start, no reference, the accel option in
  * force) of every candidate schedule on this solver's batch, with its current dynamics, weights
  * and bounds, using CUDA events on `stream`, and keeps the fastest. Candidates: family 0 with
- * item_scale 0, 2 and 8; family 3 where the instances fit; family 2 with 1 and 2 CTAs per SM
- * where the batch allows it. The
+ * item_scale 0, 2 and 8; family 3 where the instances fit; family 4 for stage-invariant
+ * batches; family 2 with 1 and 2 CTAs per SM where the batch allows it. The
  * chosen schedule and its time (ms, the second of two trial solves) are returned through the
  * pointers (host memory, any may be NULL). The stage cache and the iterates are rebuilt as for
  * pimpc_set_schedule. Blocks the host until the trials finish.

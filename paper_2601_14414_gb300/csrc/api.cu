@@ -131,8 +131,12 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   const size_t ts = tsize(precision);
   const std::vector<int> &nx = s->nx, &nu = s->nu, &N = s->N;
   if (sc.family < 0) sc.family = 0;  // lane groups; halo tiles are chosen explicitly or by the autotuner
-  if (sc.family != 0 && sc.family != 2 && sc.family != 3) {
-    why = "schedule family must be 0, 2 or 3";
+  if (sc.family != 0 && sc.family != 2 && sc.family != 3 && sc.family != 4) {
+    why = "schedule family must be 0, 2, 3 or 4";
+    return PIMPC_EINVAL;
+  }
+  if (sc.family == 4 && !lti) {
+    why = "the contraction schedule serves stage-invariant instances";
     return PIMPC_EINVAL;
   }
   if (sc.family == 2 && (precision != PIMPC_F32 || lti)) {
@@ -165,7 +169,46 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   int bps = 0;
   cudaError_t e = cudaSuccess;
-  if (tiled == 2) {
+  if (sc.family == 4) {
+    // Blocks of LB stages (LB from the shared-memory budget of cps CTAs per SM); an item holds
+    // several consecutive blocks, so the instance's matrices are expanded once per item.
+    const int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 1;
+    int64_t budget = (int64_t)smem_sm / cps - 1024 - 256;
+    budget = std::min<int64_t>(budget, optin - 256);
+    int mnu = 1;
+    for (int j = 0; j < batch; ++j) mnu = std::max(mnu, nu[j]);
+    const int LB = gemm_plan(s->max_n, s->max_nx, mnu, precision, (size_t)budget, s->gemm_plan);
+    if (LB == 0) {
+      why = "the contraction schedule needs more shared memory than the budget";
+      return PIMPC_EINVAL;
+    }
+    const int LBi = sc.item_scale > 0 ? std::min(LB, sc.item_scale) : LB;
+    s->gemm_plan[0] = LBi;
+    int64_t blocks = 0;
+    for (int j = 0; j < batch; ++j) blocks += (N[j] + LBi - 1) / LBi;
+    // about four items per SM per iteration, at least one block each
+    const int per_item = (int)std::max<int64_t>(1, blocks / (4 * (int64_t)nsm * cps));
+    for (int j = 0; j < batch; ++j) {
+      const int n = nx[j] + nu[j];
+      W[j] = block_words(nx[j], nu[j]);
+      blk[j] = tot_blk;
+      tot_blk += ((int64_t)blocks_per_instance(lti, N[j]) * W[j] + 31) / 32 * 32;
+      Ni[j] = tot_Ni;
+      tot_Ni += ((int64_t)N[j] * admm_iter_stride(n, precision) + 31) / 32 * 32;
+    }
+    for (int oi = 0; oi < batch; ++oi) {
+      const int j = order[oi];
+      for (int a0 = 0; a0 < N[j]; a0 += LBi * per_item) {
+        item_inst.push_back(j);
+        item_a.push_back(a0);
+        item_b.push_back(std::min(N[j], a0 + LBi * per_item));
+        nitems_inst[j] += 1;
+      }
+    }
+    P.threads = gemm_threads();
+    s->smem_admm = (size_t)s->gemm_plan[4];
+    e = gemm_configure(precision, s->smem_admm, &bps);
+  } else if (tiled == 2) {
     // Shared-memory budget of one CTA, and per instance the widest tile that fits it.
     const int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 2;
     int64_t D = (int64_t)smem_sm / cps - 1024 - 256;
@@ -419,6 +462,7 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
     return fail(s, PIMPC_ESTATE, "momentum table shorter than max_iters");
   PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st)
                  : s->sched.family == 3 ? launch_resident(a, s->prec, s->res_plan, s->smem_admm, st)
+                 : s->sched.family == 4 ? launch_gemm(a, s->prec, s->gemm_plan, st)
                                         : launch_admm(a, s->prec, st),
               "solve");
   s->solved = true;

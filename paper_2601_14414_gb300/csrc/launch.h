@@ -61,12 +61,19 @@ size_t res_plan(int batch, const int *nx, const int *nu, const int *N, const int
 cudaError_t launch_resident(const AdmmLaunch &s, int precision, const int *plan, size_t smem,
                             cudaStream_t stream);
 
+// Stage-invariant instances as dense contractions (register-tiled products over stage blocks).
+int gemm_threads();
+int gemm_plan(int max_n, int max_nx, int max_nu, int precision, size_t budget, int *plan);
+cudaError_t gemm_configure(int precision, size_t smem, int *blocks_per_sm);
+cudaError_t launch_gemm(const AdmmLaunch &s, int precision, const int *plan, cudaStream_t stream);
+
 // Schedule of the batched solve: which kernel family and how its work is cut.
 struct Schedule {
   int family = -1;       // 0: lane groups on plain stage blocks; 2: one thread per stage on halo
                          // tiles (stage-varying FP32 only); 3: every instance resident in the
                          // shared memory of one CTA or a cluster (item_scale = CTAs per
-                         // instance, 0: the fewest that fit); -1: the default for the batch
+                         // instance, 0: the fewest that fit); 4: stage-invariant instances as
+                         // dense contractions over blocks of stages; -1: the default
   int ctas_per_sm = 0;   // halo tiles: CTAs per SM the shared-memory budget is sized for (0: 2)
   int item_scale = 0;    // lane groups: sub-chunks per item (0: automatic);
                          // halo tiles: at most this many tiles per item (0: 4)

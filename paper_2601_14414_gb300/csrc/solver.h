@@ -11,6 +11,7 @@ struct pimpc_solver {
   std::vector<int> nx, nu, N, W, tw;
   pimpc::Schedule sched{};
   int res_plan[6] = {0, 0, 0, 0, 0, 0};   // resident schedule: cluster size and smem regions
+  int gemm_plan[5] = {0, 0, 0, 0, 0};     // contraction schedule: stages per item, padding
   double *coef_tab = nullptr;             // momentum factors by streak length (resident)
   int coef_len = 0;
   std::vector<void *> lay_allocs;   // buffers whose size depends on the schedule

@@ -1,9 +1,9 @@
 // tune.cu -- schedules of the batched solve and the autotuner that picks one by timing.
 //
 // A schedule fixes how the persistent solve cuts its work: the kernel family (lane groups on
-// plain stage blocks, or one thread per stage on halo tiles), the shared-memory budget of a CTA
-// (CTAs per SM) and the item size (sub-chunks per item for lane groups, tiles per item for halo
-// tiles). Changing the schedule changes the data layout, so the stage cache is rebuilt and the
+// plain stage blocks, one thread per stage on halo tiles, every instance resident in one CTA or
+// a cluster, or dense contractions over blocks of stages for stage-invariant instances), the
+// shared-memory budget of a CTA (CTAs per SM) and the item size. Changing the schedule changes the data layout, so the stage cache is rebuilt and the
 // iterates restart from zero at the next solve. The autotuner times a fixed number of
 // iterations of every candidate on the solver's own batch with CUDA events and keeps the
 // fastest.
@@ -65,6 +65,11 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
   {
     Schedule c;
     c.family = 3;  // resident: skipped below when the instances do not fit
+    cands.push_back(c);
+  }
+  if (s->lti) {
+    Schedule c;
+    c.family = 4;  // stage-invariant instances as dense contractions
     cands.push_back(c);
   }
   if (s->prec == PIMPC_F32 && !s->lti)

@@ -330,3 +330,56 @@ def test_resident_graph_and_adjoint():
     st = pimpc.pimpc_get_graph_stats(s.h)
     assert st["refused"] is None and st["captures"] == 1 and st["replays"] == 1, st
     assert np.array_equal(u.cpu().numpy(), np.concatenate([v.ravel() for v in base["u"]]))
+
+
+# ---- stage-invariant instances as dense contractions ---------------------------------------
+
+def lti_batch(seed, dims):
+    return [W.plain_lti(seed=seed * 100 + i, nx=nx, nu=nu, N=N) for i, (nx, nu, N) in enumerate(dims)]
+
+
+LTI_DIMS = [(4, 2, 20), (48, 16, 75), (3, 1, 1), (12, 4, 130), (7, 5, 34)]
+
+
+@pytest.mark.parametrize("accel,items", [(0, 0), (1, 0), (1, 5)])
+def test_contraction_fp64_matches_oracle(accel, items):
+    insts = lti_batch(71, LTI_DIMS)
+    s = pimpc.Solver(insts, precision=pimpc.F64, eps=-1.0, max_iters=120, accel=accel)
+    s.set_schedule(4, 0, items)
+    res = s.solve()
+    its = s.iterates()
+    ora = oracle.solve_batch(insts, eps=-1.0, max_iters=120, accel=accel)
+    for j, o in enumerate(ora):
+        for key in ("z", "v", "th", "be", "la"):
+            assert relerr(its[j][key], o[key]) <= 1e-10, (j, key)
+        assert relerr(res["u"][j], o["u"]) <= 1e-10
+
+
+def test_contraction_fp32_and_warm_start():
+    insts = lti_batch(72, LTI_DIMS)
+    s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=150, accel=0)
+    s.set_schedule(4)
+    res = s.solve()
+    ora = oracle.solve_batch(insts, eps=-1.0, max_iters=150, accel=0)
+    for j, o in enumerate(ora):
+        assert relerr(res["u"][j], o["u"]) <= 1e-4, j
+        assert relerr(res["x"][j], o["x"]) <= 1e-4, j
+    d = pimpc.Solver(insts, precision=pimpc.F64, eps=-1.0, max_iters=40, accel=1)
+    d.set_schedule(4, 0, 7)
+    d.solve()
+    first = d.iterates()
+    d.solve(warm_start=2)
+    its = d.iterates()
+    for j, inst in enumerate(insts):
+        warm = {k: np.concatenate([first[j][k][1:], first[j][k][-1:]], axis=0)
+                for k in ("z", "v", "th", "be", "la")}
+        o = oracle.solve(inst, eps=-1.0, max_iters=40, accel=1, warm=warm)
+        assert relerr(its[j]["z"], o["z"]) <= 1e-10, j
+
+
+def test_contraction_rejects_stage_varying_batches():
+    s = pimpc.Solver(ragged_batch(73, dims=[(4, 2, 10)]), precision=pimpc.F32, eps=-1.0,
+                     max_iters=5, accel=0)
+    with pytest.raises(pimpc.PimpcError) as e:
+        s.set_schedule(4)
+    assert e.value.code == pimpc.EINVAL
