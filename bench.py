@@ -53,6 +53,25 @@ def parse_args():
     return ap.parse_args()
 
 
+def rank_seed(seed, rank):
+    """Every rank solves its own seeded batch (weak scaling: independent instances)."""
+    return seed + 7919 * rank
+
+
+def combine_ranks(torch, dist, dev, ms, ok, iters, stage_iters):
+    """Whole-job figures from every rank's step time and counts: the slowest rank's time and
+    the sums of accurate solves, instance-iterations and stage-iterations (no collective on the
+    data path; one gather of four numbers after the timed region)."""
+    if dist is None:
+        return ms, float(ok), float(iters), float(stage_iters)
+    t = torch.tensor([ms, float(ok), iters, stage_iters], dtype=torch.float64, device=dev)
+    allt = [torch.zeros_like(t) for _ in range(dist.get_world_size())]
+    dist.all_gather(allt, t)
+    allt = torch.stack(allt).cpu().numpy()
+    return (float(allt[:, 0].max()), float(allt[:, 1].sum()), float(allt[:, 2].sum()),
+            float(allt[:, 3].sum()))
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -463,7 +482,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
 
-    insts = W.batched_uneven(seed=cfg["seed"] + 7919 * rank, batch=batch)
+    insts = W.batched_uneven(seed=rank_seed(cfg["seed"], rank), batch=batch)
     p = pimpc.pack(insts)
     nx, nu, N = p["nx"].astype(np.int64), p["nu"].astype(np.int64), p["N"].astype(np.int64)
     d = {k: torch.from_numpy(p[k]).to(dev) for k in ("A", "B", "e", "x0", "ref")}
@@ -561,16 +580,8 @@ def run_ours(args):
     ok = int(np.sum(err <= cfg["accuracy"]))
 
     ms_step = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step, ok, float(np.sum(iters)), float(np.sum(iters * N))],
-                         dtype=torch.float64, device=dev)
-        allt = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(allt, t)
-        allt = torch.stack(allt).cpu().numpy()
-        ms_max = float(allt[:, 0].max())
-        ok_all, it_all, stit_all = (float(allt[:, i].sum()) for i in (1, 2, 3))
-    else:
-        ms_max, ok_all, it_all, stit_all = ms_step, ok, float(np.sum(iters)), float(np.sum(iters * N))
+    ms_max, ok_all, it_all, stit_all = combine_ranks(
+        torch, dist, dev, ms_step, ok, float(np.sum(iters)), float(np.sum(iters * N)))
     value = ok_all / (ms_max / 1e3)
 
     # Roofline of the dominant kernel (the ADMM solve), bytes per launch / launch time.
