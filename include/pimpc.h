@@ -51,6 +51,7 @@ enum { PIMPC_MODEL_QUADROTOR = 0, PIMPC_MODEL_CARTPOLE = 1, PIMPC_MODEL_CSTR = 2
 /* Size limits of one instance. */
 #define PIMPC_MAX_N_LTV 32   /* n = nx + nu for stage-varying dynamics   */
 #define PIMPC_MAX_N_LTI 64   /* n = nx + nu for stage-invariant dynamics */
+#define PIMPC_MAX_NU 32      /* nu (inputs per stage), any dynamics      */
 
 typedef struct pimpc_solver pimpc_solver;
 
@@ -58,7 +59,7 @@ typedef struct pimpc_solver pimpc_solver;
  * pimpc_create -- setup(model dims, N): allocate a solver for `batch` independent instances.
  *   nx[batch], nu[batch], N[batch]  host arrays: state size (>= 1), input size (>= 1) and horizon
  *                                   (>= 1) of each instance; n = nx + nu <= PIMPC_MAX_N_LTV
- *                                   (lti = 0) or PIMPC_MAX_N_LTI (lti = 1).
+ *                                   (lti = 0) or PIMPC_MAX_N_LTI (lti = 1), nu <= PIMPC_MAX_NU.
  *   lti        1: one (A, B, e) per instance used at every stage; 0: one triple per stage.
  *   precision  PIMPC_F32 or PIMPC_F64 arithmetic for the iterations.
  *   device     CUDA device ordinal.

@@ -630,10 +630,11 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   if (lti != 0 && lti != 1) { g_create_error = "lti must be 0 or 1"; return PIMPC_EINVAL; }
   const int nmax = lti ? PIMPC_MAX_N_LTI : PIMPC_MAX_N_LTV;
   for (int j = 0; j < batch; ++j) {
-    if (nx[j] < 1 || nu[j] < 1 || N[j] < 1 || nx[j] + nu[j] > nmax) {
-      char b[160];
-      snprintf(b, sizeof b, "instance %d: need nx >= 1, nu >= 1, N >= 1, nx + nu <= %d (got %d, %d, %d)",
-               j, nmax, nx[j], nu[j], N[j]);
+    if (nx[j] < 1 || nu[j] < 1 || N[j] < 1 || nx[j] + nu[j] > nmax || nu[j] > PIMPC_MAX_NU) {
+      char b[200];
+      snprintf(b, sizeof b,
+               "instance %d: need nx >= 1, 1 <= nu <= %d, N >= 1, nx + nu <= %d (got %d, %d, %d)",
+               j, PIMPC_MAX_NU, nmax, nx[j], nu[j], N[j]);
       g_create_error = b;
       return PIMPC_EINVAL;
     }

@@ -48,6 +48,11 @@ def test_create_rejects_bad_sizes_before_touching_a_device():
     assert rc == pimpc.EINVAL
     rc = lib.pimpc_create(1, nx.ctypes.data, nu.ctypes.data, N.ctypes.data, 0, 7, 0, ctypes.byref(h))
     assert rc == pimpc.EINVAL
+    # stage-invariant data allows n = nx + nu up to 64, but nu stays within one warp's lanes
+    nx1, nu1, N1 = (np.array([v], np.int32) for v in (20, 33, 10))
+    rc = lib.pimpc_create(1, nx1.ctypes.data, nu1.ctypes.data, N1.ctypes.data, 1, 0, 0, ctypes.byref(h))
+    assert rc == pimpc.EINVAL and not h.value
+    assert b"nu <= 32" in lib.pimpc_last_error(None)
 
 
 def test_pack_layout_is_batch_then_stage_major():
