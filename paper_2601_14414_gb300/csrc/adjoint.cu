@@ -26,9 +26,9 @@
 // Work. One CTA per instance (largest instances first), one thread per stage (threads loop when
 // N exceeds the block). All per-stage vectors live in a workspace in global memory, component
 // major ([component][stage]), so that a warp's accesses to one component are coalesced; the
-// stage matrices are read from the solve's stage data in either of its layouts (plain blocks:
-// G with odd row stride, symmetric H and M as wrapped diagonals; halo tiles: element-major
-// slots, H and M packed). Adjoint arithmetic runs in the iteration precision T; the per-stage
+// stage matrices are read from the solve's stage data in any of its layouts (plain blocks:
+// G with odd row stride, symmetric H and M as wrapped diagonals; blocked: H as wrapped 4 x 4
+// block diagonals; halo tiles: element-major slots, H and M packed). Adjoint arithmetic runs in the iteration precision T; the per-stage
 // gradient sums run in FP64. No thread waits on another CTA: only __syncthreads separates phases.
 #include <algorithm>
 #include <vector>
@@ -88,8 +88,9 @@ struct Inst {
     return blk + (lti ? 0 : (int64_t)k * W);
   }
   __device__ int es() const { return tiled == 2 ? tw : 1; }
-  // G_k(r, c), e_k(r), H_k(r, c), M_k(r, c) in either layout (plain: G rows of stride ld, H and M
-  // as wrapped diagonals; halo tiles: G row-major, H and M packed lower).
+  // G_k(r, c), e_k(r), H_k(r, c), M_k(r, c) in any layout (plain and blocked: G rows of stride
+  // ld, M as wrapped diagonals, H as wrapped diagonals or wrapped 4 x 4 block diagonals; halo
+  // tiles: G row-major, H and M packed lower).
   __device__ T Gv(int k, int r, int c) const {
     return tiled == 2 ? slot(k)[(r * n + c) * tw] : slot(k)[r * ld + c];
   }
@@ -114,6 +115,22 @@ __device__ __forceinline__ T sym_at(const T *Wp, int m, int r, int c) {
   return (2 * d <= m) ? Wp[d * m + r] : Wp[(m - d) * m + c];
 }
 
+// Element (r, c) of a symmetric m x m matrix stored as wrapped 4 x 4 block diagonals (block
+// (d, I) = S_{I, (I+d) mod nb} for d <= nb / 2).
+template <typename T>
+__device__ __forceinline__ T sym_block_at(const T *Hb, int m, int r, int c) {
+  const int nb = bl_nb(m);
+  int I = r >> 2, a = r & 3, J = c >> 2, b = c & 3;
+  int d = J - I;
+  if (d < 0) d += nb;
+  if (2 * d > nb) {  // stored as the transpose: block (nb - d, J), element (b, a)
+    d = nb - d;
+    int t = I; I = J; J = t;
+    t = a; a = b; b = t;
+  }
+  return Hb[bl_sym_index(nb, d, I, a, b)];
+}
+
 template <typename T>
 __device__ T Inst<T>::Hv(int k, int r, int c) const {
   if (tiled == 2) {
@@ -121,7 +138,7 @@ __device__ T Inst<T>::Hv(int k, int r, int c) const {
     return slot(k)[(nx * n + nx + i * (i + 1) / 2 + q) * tw];
   }
   const T *b = blk + (lti ? ((k < N - 1) ? 0 : W) : (int64_t)k * W) + oH;
-  return sym_at(b, n, r, c);
+  return tiled == 3 ? sym_block_at(b, n, r, c) : sym_at(b, n, r, c);
 }
 
 template <typename T>
@@ -139,15 +156,16 @@ __device__ void make_inst(const AdjArgs &a, int j, Inst<T> &I) {
   I.nu = a.L.nu[j];
   I.n = I.nx + I.nu;
   I.N = a.L.N[j];
-  I.ld = odd_ld(I.n);
+  const int ts = (int)sizeof(T);
+  I.ld = a.L.tiled == 3 ? bl_ldg(I.n, ts) : odd_ld(I.n);
   I.W = a.L.W[j];
   I.lti = a.L.lti;
   I.tiled = a.L.tiled;
   I.tw = a.L.tiled == 2 ? a.L.tw[j] : 0;
   I.blk = (const T *)a.blk + a.L.blk[j];
   I.oE = I.nx * I.ld;
-  I.oH = I.oE + I.nx;
-  I.oM = I.oH + wrapped_size(I.n);
+  I.oH = a.L.tiled == 3 ? bl_oH(I.nx, I.nu, ts) : I.oE + I.nx;
+  I.oM = a.L.tiled == 3 ? bl_oM(I.nx, I.nu, ts) : I.oH + wrapped_size(I.n);
   I.qd = (const T *)a.qd + a.L.off_n[j];
   I.ref = a.ref ? (const T *)a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j]) : nullptr;
   I.refstride = a.ref_per_stage ? I.n : 0;

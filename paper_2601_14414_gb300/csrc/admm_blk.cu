@@ -1,0 +1,501 @@
+// admm_blk.cu -- Algorithm 1 with lanes that own 4-column blocks, on blocked stage blocks
+// (schedule family 5, tiled layout 3).
+//
+// The frame is the lock-step persistent one of admm.cu (items of consecutive stages pulled from
+// a queue, a grid barrier per iteration, the instance's last item applying steps 5-7, stopped
+// instances compacted away). What differs is how a stage's products map onto lanes.
+//
+// A group of g = 4, 8 or 16 lanes (n <= 16, 32, 64) handles one stage; lane l owns the
+// components 4l .. 4l+3 of every stage vector and reads and writes them as 16-byte vectors. The
+// products of Algorithm 1 become, per lane, dense 4-wide work:
+//   * q_k = Abar_k^T y_k and t_k = B_k^T w_x + w_u (y = zhat - vhat + lambdahat - ebar,
+//     w = vhat - betahat, both of stage k) in one pass over the rows of G_k: lane l reads row r's
+//     block l and accumulates both. q_k enters h_{k-1}, so the group of stage k-1 reads it;
+//   * du_k = M_k t_k (M as scalar wrapped diagonals, one lane per input);
+//   * xbar_{k+1} = H_k h_k with H_k stored as wrapped 4 x 4 block diagonals: lane l owns block
+//     row l and, per block diagonal d, applies block (l, l+d) and the transpose of block
+//     (l-d, l), so every lane runs the same code and every read is a 16-byte vector;
+//   * Abar_k xbar_k and B_k du_k by rows (lane l owns rows l, l+g, ...).
+// A sub-chunk holds S - 1 stages and the next stage, whose group only forms q (the first stage
+// of the next sub-chunk is formed again there). The group left over in the xbar phase of an
+// item's first sub-chunk recomputes xbar_a = H_{a-1} h_{a-1} from the halo (the hats of stage
+// a-1 and H_{a-1}; q_a comes from the group of stage a).
+//
+// Data movement as in admm.cu: one cp.async.bulk batch per sub-chunk completing on an mbarrier
+// (stage blocks, the next stage's G and e, current and previous iterates, the halo); every wait
+// is bounded. The number of groups S of an instance is fixed on the host so that the
+// sub-chunk's shared memory fits the budget of the requested CTAs per SM.
+#include <math.h>
+
+#include <algorithm>
+
+#include "bulk.cuh"
+#include "lockstep.cuh"
+#include "products.cuh"
+
+namespace pimpc {
+
+namespace {
+
+using ls::kWaitLimit;
+using namespace bulk;
+
+template <typename T>
+using Args = ls::Args<T>;
+
+constexpr int kThreads = 128;
+
+template <typename T>
+struct V4 {
+  T v[4];
+};
+
+__device__ __forceinline__ V4<float> ld4(const float *p) {
+  const float4 q = *reinterpret_cast<const float4 *>(p);
+  return {{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double *p) {
+  const double2 q0 = *reinterpret_cast<const double2 *>(p);
+  const double2 q1 = *reinterpret_cast<const double2 *>(p + 2);
+  return {{q0.x, q0.y, q1.x, q1.y}};
+}
+__device__ __forceinline__ void st4(float *p, const V4<float> &x) {
+  *reinterpret_cast<float4 *>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const V4<double> &x) {
+  *reinterpret_cast<double2 *>(p) = make_double2(x.v[0], x.v[1]);
+  *reinterpret_cast<double2 *>(p + 2) = make_double2(x.v[2], x.v[3]);
+}
+template <typename T>
+__device__ __forceinline__ V4<T> zero4() {
+  return {{(T)0, (T)0, (T)0, (T)0}};
+}
+
+// Shared-memory regions of a sub-chunk with S groups (elements of T): LTV stage blocks (S - 1
+// blocks and the next stage's G and e), current and previous iterates (S records each), the
+// halo (H_{a-1}, or both blocks of a stage-invariant instance), the halo iterates, per-group
+// scratch (5 vectors) and the xbar rows (double-buffered, S rows each).
+struct Regions {
+  int rawI, capI, haloB, haloI, scr, X, total;
+};
+
+__host__ __device__ inline Regions regions(int nx, int nu, int lti, int tsize, int S) {
+  const int n = nx + nu, nP = bl_pad4(n), rec = bl_rec(n);
+  const int W = bl_block_words(nx, nu, tsize), ge = bl_oH(nx, nu, tsize);
+  Regions r;
+  r.rawI = lti ? 0 : bl_pad4((S - 1) * W + ge);
+  r.capI = S * rec;
+  r.haloB = r.rawI + 2 * r.capI;
+  r.haloI = r.haloB + bl_pad4(lti ? 2 * W : bl_sym_words(n));
+  r.scr = r.haloI + 2 * rec;
+  r.X = r.scr + S * 5 * nP;
+  r.total = r.X + 2 * S * nP;
+  return r;
+}
+
+// (S h) restricted to the rows 4 I .. 4 I + 3, S symmetric in wrapped 4 x 4 block diagonals at
+// Hb (nb blocks per row, D = nb/2 + 1 block diagonals), h in shared memory (4 nb values).
+template <typename T>
+__device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int D, int I) {
+  V4<T> acc = zero4<T>();
+  const int rs = D * nb * 4;  // distance between the planes of rows a and a + 1
+  int Jp = I, Jm = I;
+  for (int d = 0; d < D; ++d) {
+    const T *bd = Hb + d * nb * 4;
+    {  // block (I, I + d): rows of the block against h_{I+d}
+      const V4<T> hv = ld4(h + 4 * Jp);
+      const T *bp = bd + I * 4;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const V4<T> row = ld4(bp + a * rs);
+        acc.v[a] += row.v[0] * hv.v[0] + row.v[1] * hv.v[1] + row.v[2] * hv.v[2] + row.v[3] * hv.v[3];
+      }
+    }
+    if (d > 0 && 2 * d != nb) {  // block (I, I - d) = transpose of block (I - d, I)
+      const V4<T> hm = ld4(h + 4 * Jm);
+      const T *bm = bd + Jm * 4;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const V4<T> row = ld4(bm + a * rs);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc.v[b] += row.v[b] * hm.v[a];
+      }
+    }
+    Jp = (Jp + 1 == nb) ? 0 : Jp + 1;
+    Jm = (Jm == 0) ? nb - 1 : Jm - 1;
+  }
+  return acc;
+}
+
+template <typename T>
+__device__ inline T clampv(T x, T lo, T hi) {
+  return x < lo ? lo : (x > hi ? hi : x);
+}
+
+// Momentum hat of four components: cur + f (cur - prev).
+template <typename T>
+__device__ __forceinline__ V4<T> hat4(const T *cur, const T *prev, bool use_prev, T f) {
+  V4<T> x = ld4(cur);
+  if (use_prev) {
+    const V4<T> p = ld4(prev);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x.v[i] += f * (x.v[i] - p.v[i]);
+  }
+  return x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int sItem, sOk, sArr;
+  __shared__ double sRed[kThreads / 32];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  constexpr int TS = (int)sizeof(T);
+  const int tid = threadIdx.x;
+  const unsigned nblocks = gridDim.x;
+  Ctl *ctl = a.ctl;
+  const int lti = a.L.lti;
+
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t par = 0u;
+  bool pend = false;
+
+  int cl = 0;
+  for (int it = 0; it < a.max_iters; ++it) {
+    const int nact = *(volatile int *)&ctl->nlist[cl];
+    bool ok = true;
+    for (;;) {
+      if (tid == 0) sItem = atomicAdd(&ctl->queue[it & 1], 1);
+      __syncthreads();
+      const int q = sItem;
+      __syncthreads();
+      if (q >= nact) break;
+      const int item = a.list[cl][q];
+      const int j = a.item_inst[item];
+      if (*(volatile int *)&a.stop[j]) continue;
+      const int ka = a.item_a[item], kb = a.item_b[item];
+      const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j], n = nx + nu;
+      const int g = bl_group(n), S = a.grp[j], P = S - 1;
+      const int nP = bl_pad4(n), rec = bl_rec(n), nb = bl_nb(n), D = bl_diags(nb);
+      const int ldg = bl_ldg(n, TS), oE = bl_oE(nx, nu, TS), oH = bl_oH(nx, nu, TS);
+      const int oM = bl_oM(nx, nu, TS), symW = bl_sym_words(n);
+      const int W = a.L.W[j];
+      const Regions R = regions(nx, nu, lti, TS, S);
+      const int bse = a.base[j];
+      const int64_t ib = a.L.Ni[j];
+      const T *Ic = a.it[(bse + it) % 3] + ib;
+      const T *Ip = a.it[(bse + it + 2) % 3] + ib;
+      T *In = a.it[(bse + it + 1) % 3] + ib;
+      const T *blk = a.blk + a.L.blk[j];
+      const double coefd = *(volatile double *)&a.coef[j];
+      const T f = (T)coefd;
+      const bool use_prev = coefd != 0.0;
+      const T rho = (T)a.rho;
+      const T *qd = a.qd + a.L.off_n[j];
+      const T *ref = a.ref ? (a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j])) : nullptr;
+      const int refstride = a.ref_per_stage ? n : 0;
+      const T *lo = a.lo + a.L.off_n[j], *hi = a.hi + a.L.off_n[j];
+      const int grp = tid / g, l = tid - grp * g;
+      const int c0 = 4 * l;
+      const bool own = c0 < n;
+      // this group's scratch (only touched when grp < S): y / h / Abar xbar, w / B du, q, t, du
+      T *scr = sm + R.scr + grp * 5 * nP;
+      T *sY = scr, *sW = scr + nP, *sQ = scr + 2 * nP, *sT = scr + 3 * nP, *sDU = scr + 4 * nP;
+      T *rB = sm;
+      const T *rIc = sm + R.rawI, *rIp = sm + R.rawI + R.capI;
+      T *hB = sm + R.haloB, *hI = sm + R.haloI;
+      const T *ltiB = hB;  // stage-invariant: block 0 (H_k, k < N-1) then block 1 (H_{N-1})
+      T cacc = (T)0;
+
+      // Copies of the sub-chunk that starts at stage k0 (thread 0 issues).
+      auto issue = [&](int k0, bool first) {
+        const int cnt = min(P, kb - k0);
+        const int la = (k0 + cnt < N) ? 1 : 0;  // the next stage: its G and e only
+        const int ns = cnt + la;
+        const bool halo = first && ka > 0;
+        const uint32_t it_bytes = (uint32_t)(ns * rec * TS);
+        const uint32_t blk_bytes = (uint32_t)((cnt * W + la * oH) * TS);
+        uint32_t bytes = it_bytes * (use_prev ? 2u : 1u);
+        if (!lti) bytes += blk_bytes;
+        if (halo) {
+          bytes += (uint32_t)(rec * TS) * (use_prev ? 2u : 1u);
+          if (!lti) bytes += (uint32_t)(symW * TS);
+        }
+        if (lti && first) bytes += (uint32_t)(2 * W * TS);
+        fence_proxy_async();
+        mbar_expect_tx(&mbar, bytes);
+        if (!lti) bulk_load(rB, blk + (int64_t)k0 * W, blk_bytes, &mbar);
+        bulk_load(sm + R.rawI, Ic + (int64_t)k0 * rec, it_bytes, &mbar);
+        if (use_prev) bulk_load(sm + R.rawI + R.capI, Ip + (int64_t)k0 * rec, it_bytes, &mbar);
+        if (halo) {
+          if (!lti) bulk_load(hB, blk + (int64_t)(ka - 1) * W + oH, (uint32_t)(symW * TS), &mbar);
+          bulk_load(hI, Ic + (int64_t)(ka - 1) * rec, (uint32_t)(rec * TS), &mbar);
+          if (use_prev) bulk_load(hI + rec, Ip + (int64_t)(ka - 1) * rec, (uint32_t)(rec * TS), &mbar);
+        }
+        if (lti && first) bulk_load(hB, blk, (uint32_t)(2 * W * TS), &mbar);
+      };
+
+      const int nsub = (kb - ka + P - 1) / P;
+      if (tid == 0) issue(ka, true);
+      pend = true;
+      for (int sc = 0; sc < nsub; ++sc) {
+        const int k0 = ka + sc * P;
+        const int cnt = min(P, kb - k0);
+        const bool la = k0 + cnt < N;
+        if (sc > 0) {  // the single buffer is free after the previous sub-chunk's last barrier
+          if (tid == 0) issue(k0, false);
+          pend = true;
+        }
+        if (tid == 0) sArr = mbar_wait(&mbar, par, ctl) ? 1 : 0;
+        __syncthreads();
+        const bool arrived = sArr != 0;
+        if (arrived) {
+          par ^= 1u;
+          pend = false;
+        } else {
+          ok = false;  // the copy may still be in flight: it stays pending for the exit wait
+        }
+        T *Xc = sm + R.X + (sc & 1) * S * nP;
+        T *Xn = sm + R.X + ((sc & 1) ^ 1) * S * nP;
+        const int k = k0 + grp;
+        const bool stage = arrived && grp < cnt;           // stage k of this sub-chunk
+        const bool look = arrived && grp == cnt && la;     // the next stage: q only
+        const bool hgrp = arrived && sc == 0 && ka > 0 && grp == S - 1;  // recomputes xbar_a
+        const T *Gk = lti ? ltiB : rB + grp * W;
+        const T *hc = rIc + grp * rec, *hp = rIp + grp * rec;
+
+        // ---- phase 1: hats, y and w; q and t in one pass over G_k; du = M t ----
+        V4<T> zh = zero4<T>(), vh = zero4<T>(), th = zero4<T>(), bh = zero4<T>(), lh = zero4<T>();
+        V4<T> e4 = zero4<T>(), y4 = zero4<T>(), w4 = zero4<T>();
+        if ((stage || look) && own) {
+          zh = hat4(hc + c0, hp + c0, use_prev, f);
+          vh = hat4(hc + nP + c0, hp + nP + c0, use_prev, f);
+          lh = hat4(hc + 4 * nP + c0, hp + 4 * nP + c0, use_prev, f);
+          if (stage) {
+            th = hat4(hc + 2 * nP + c0, hp + 2 * nP + c0, use_prev, f);
+            bh = hat4(hc + 3 * nP + c0, hp + 3 * nP + c0, use_prev, f);
+          }
+          if (c0 < nx) e4 = ld4(Gk + oE + c0);  // zero beyond nx (padding)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            y4.v[i] = zh.v[i] - vh.v[i] + lh.v[i] - e4.v[i];
+            w4.v[i] = vh.v[i] - bh.v[i];
+          }
+          st4(sY + c0, y4);
+          st4(sW + c0, w4);
+          st4(sDU + c0, zero4<T>());
+        }
+        if (sc == 0 && ka == 0)
+          for (int c = tid; c < nP; c += kThreads) Xc[c] = c < n ? a.xb0[a.L.off_n[j] + c] : (T)0;
+        __syncwarp();
+        if ((stage || look) && own) {
+          V4<T> qv = zero4<T>(), tv = zero4<T>();
+          const T *gc = Gk + c0;
+          int r = 0;
+          for (; r + 3 < nx; r += 4) {
+            const V4<T> yv = ld4(sY + r), wv = ld4(sW + r);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const V4<T> gr = ld4(gc + (r + u) * ldg);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                qv.v[i] += gr.v[i] * yv.v[u];
+                tv.v[i] += gr.v[i] * wv.v[u];
+              }
+            }
+          }
+          for (; r < nx; ++r) {
+            const T yr = sY[r], wr = sW[r];
+            const V4<T> gr = ld4(gc + r * ldg);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              qv.v[i] += gr.v[i] * yr;
+              tv.v[i] += gr.v[i] * wr;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (c0 + i >= nx) {  // the identity rows of Abar, and w_u in t
+              qv.v[i] += y4.v[i];
+              tv.v[i] += w4.v[i];
+            }
+          st4(sQ + c0, qv);
+          st4(sT + c0, tv);
+        }
+        __syncwarp();
+        if (stage)
+          for (int jj = l; jj < nu; jj += g) sDU[nx + jj] = sym_wrapped(Gk + oM, sT + nx, nu, jj);
+        if (!__syncthreads_and(arrived)) { ok = false; break; }  // uniform across the CTA
+
+        // ---- phase 2: h_k (with q_{k+1} of the next group) and xbar_{k+1} = H_k h_k ----
+        if (stage && own) {
+          V4<T> qn = zero4<T>();
+          if (k + 1 < N) qn = ld4(scr + 5 * nP + 2 * nP + c0);  // the next group's q
+          V4<T> h;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int c = c0 + i;
+            T v = (T)0;
+            if (c < n) {
+              const T rf = ref ? ref[(int64_t)k * refstride + c] : (T)0;
+              v = qd[c] * rf + rho * (zh.v[i] - th.v[i] + qn.v[i]);
+            }
+            h.v[i] = v;
+          }
+          st4(sY + c0, h);
+        }
+        if (hgrp && own) {  // h_{a-1} from the halo hats and q_a (group 0)
+          const V4<T> zm = hat4(hI + c0, hI + rec + c0, use_prev, f);
+          const V4<T> tm = hat4(hI + 2 * nP + c0, hI + rec + 2 * nP + c0, use_prev, f);
+          const V4<T> qa = ld4(sm + R.scr + 2 * nP + c0);
+          V4<T> h;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int c = c0 + i;
+            T v = (T)0;
+            if (c < n) {
+              const T rf = ref ? ref[(int64_t)(ka - 1) * refstride + c] : (T)0;
+              v = qd[c] * rf + rho * (zm.v[i] - tm.v[i] + qa.v[i]);
+            }
+            h.v[i] = v;
+          }
+          st4(sY + c0, h);
+        }
+        __syncwarp();
+        if ((stage || hgrp) && l < nb) {
+          const T *Hb = stage ? (lti ? ltiB + ((k < N - 1) ? 0 : W) + oH : rB + grp * W + oH)
+                              : (lti ? ltiB + oH : hB);
+          const V4<T> x = sym_blocks(Hb, sY, nb, D, l);
+          if (stage) {
+            st4(Xc + (grp + 1) * nP + c0, x);
+            if (grp + 1 == cnt) st4(Xn + c0, x);  // row 0 of the next sub-chunk
+          } else {
+            st4(Xc + c0, x);
+          }
+        }
+        __syncthreads();
+
+        // ---- phase 3: Abar xbar_k and B du by rows; steps 2-4 on the owned components ----
+        if (stage) {
+          const T *xk = Xc + grp * nP;
+          const int jx = nx >> 2;  // first column block that holds input columns
+          for (int r = l; r < nx; r += g) {
+            const T *row = Gk + r * ldg;
+            V4<T> ax = zero4<T>(), bd = zero4<T>();
+            for (int J = 0; J < nb; ++J) {
+              const V4<T> gr = ld4(row + 4 * J), xv = ld4(xk + 4 * J);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) ax.v[i] += gr.v[i] * xv.v[i];
+              if (J >= jx) {
+                const V4<T> dv = ld4(sDU + 4 * J);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) bd.v[i] += gr.v[i] * dv.v[i];
+              }
+            }
+            sY[r] = (ax.v[0] + ax.v[1]) + (ax.v[2] + ax.v[3]);
+            sW[r] = (bd.v[0] + bd.v[1]) + (bd.v[2] + bd.v[3]);
+          }
+        }
+        __syncwarp();
+        if (stage && own) {
+          const T *xk = Xc + grp * nP, *xk1 = Xc + (grp + 1) * nP;
+          const V4<T> x1 = ld4(xk1 + c0), x0 = ld4(xk + c0), du4 = ld4(sDU + c0);
+          const V4<T> ax4 = ld4(sY + c0), bd4 = ld4(sW + c0);
+          V4<T> oz, ov, ot, ob, ol;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int c = c0 + i;
+            if (c < n) {
+              const bool xs = c < nx;
+              const T ax = xs ? ax4.v[i] : x0.v[i];
+              const T bd = xs ? bd4.v[i] : du4.v[i];
+              const T ee = e4.v[i];
+              const T xn = x1.v[i];
+              const T gam = bd + bh.v[i] - ax - ee + lh.v[i];
+              const T w = ((T)2 * (xn + th.v[i] + ax + ee - lh.v[i]) + gam) / (T)3;
+              const T z = clampv(w, lo[c], hi[c]);
+              const T v = (T)0.5 * (z + gam);
+              const T tt = th.v[i] + xn - z;
+              const T be = bh.v[i] + bd - v;
+              const T lam = lh.v[i] + z - ax - v - ee;
+              const T d1 = tt - th.v[i], d2 = be - bh.v[i], d3 = lam - lh.v[i];
+              const T d4 = z - zh.v[i], d5 = v - vh.v[i], d6 = d4 - d5;
+              cacc += d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5 + d6 * d6;
+              oz.v[i] = z; ov.v[i] = v; ot.v[i] = tt; ob.v[i] = be; ol.v[i] = lam;
+            } else {
+              oz.v[i] = ov.v[i] = ot.v[i] = ob.v[i] = ol.v[i] = (T)0;
+            }
+          }
+          T *o = In + (int64_t)k * rec + c0;
+          st4(o, oz);
+          st4(o + nP, ov);
+          st4(o + 2 * nP, ot);
+          st4(o + 3 * nP, ob);
+          st4(o + 4 * nP, ol);
+        }
+        __syncthreads();
+      }
+      if (!ok) break;
+
+      // ---- step 4: this item's share of c; the last item of the instance applies steps 5-7 ----
+      for (int off = 16; off > 0; off >>= 1) cacc += __shfl_xor_sync(0xffffffffu, cacc, off);
+      if ((tid & 31) == 0) sRed[tid >> 5] = (double)cacc;
+      __syncthreads();
+      if (tid == 0) {
+        double part = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) part += sRed[w];
+        ls::finish_item(a, j, it, part);
+      }
+    }
+    if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
+    if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
+    if (*(volatile int *)&ctl->active <= 0) break;
+    if (!ls::compact(a, cl, nact, &sOk)) break;
+  }
+  // Never leave a bulk copy in flight into shared memory: wait (bounded) for the pending phase.
+  if (pend) {
+    long long k = 0;
+    while (!mbar_try_wait(&mbar, par) && ++k < kWaitLimit) {
+    }
+  }
+}
+
+}  // namespace
+
+int blk_threads() { return kThreads; }
+
+int64_t blk_region_words(int nx, int nu, int lti, int precision, int S) {
+  return regions(nx, nu, lti, precision == 0 ? 4 : 8, S).total;
+}
+
+cudaError_t blk_configure(int precision, size_t smem, int *blocks_per_sm) {
+  cudaError_t rc;
+  if (precision == 0) {
+    rc = cudaFuncSetAttribute(blk_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (rc != cudaSuccess) return rc;
+    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, blk_kernel<float>, kThreads, smem);
+  } else {
+    rc = cudaFuncSetAttribute(blk_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (rc != cudaSuccess) return rc;
+    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, blk_kernel<double>, kThreads, smem);
+  }
+  return rc;
+}
+
+cudaError_t launch_blk(const AdmmLaunch &s, int precision, size_t smem, cudaStream_t stream) {
+  if (precision == 0) {
+    ls::Args<float> a = ls::make_args<float>(s);
+    void *params[] = {&a};
+    return ls::launch_sequence<float>(s, a, (const void *)blk_kernel<float>, params, smem, stream);
+  }
+  ls::Args<double> a = ls::make_args<double>(s);
+  void *params[] = {&a};
+  return ls::launch_sequence<double>(s, a, (const void *)blk_kernel<double>, params, smem, stream);
+}
+
+}  // namespace pimpc

@@ -131,8 +131,8 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   const size_t ts = tsize(precision);
   const std::vector<int> &nx = s->nx, &nu = s->nu, &N = s->N;
   if (sc.family < 0) sc.family = 0;  // lane groups; halo tiles are chosen explicitly or by the autotuner
-  if (sc.family != 0 && sc.family != 2 && sc.family != 3 && sc.family != 4) {
-    why = "schedule family must be 0, 2, 3 or 4";
+  if (sc.family != 0 && sc.family != 2 && sc.family != 3 && sc.family != 4 && sc.family != 5) {
+    why = "schedule family must be 0, 2, 3, 4 or 5";
     return PIMPC_EINVAL;
   }
   if (sc.family == 4 && !lti) {
@@ -147,13 +147,15 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     why = "schedule: ctas_per_sm in 0..8, item_scale in 0..64";
     return PIMPC_EINVAL;
   }
-  const int tiled = sc.family == 2 ? 2 : 0;  // the resident family uses the plain layout
+  // halo tiles and the blocked lane groups have layouts of their own; the resident and the
+  // contraction families read the plain layout
+  const int tiled = sc.family == 2 ? 2 : (sc.family == 5 ? 3 : 0);
   s->tiled = tiled;
   int nsm = 0, smem_sm = 0, optin = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
-  std::vector<int> W(batch), tw(batch, 0);
+  std::vector<int> W(batch), tw(batch, 0), grp(batch, 0);
   std::vector<int64_t> blk(batch), Ni(batch);
   int64_t tot_blk = 0, tot_Ni = 0;
   AdmmLaunch P{};
@@ -208,6 +210,65 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     P.threads = gemm_threads();
     s->smem_admm = (size_t)s->gemm_plan[4];
     e = gemm_configure(precision, s->smem_admm, &bps);
+  } else if (tiled == 3) {
+    // Per instance the most lane groups (S - 1 stages and the next stage per sub-chunk) whose
+    // shared memory fits the budget of cps CTAs per SM; by default 3 CTAs per SM, or fewer when
+    // an instance needs it.
+    const int thr = blk_threads();
+    int64_t budget = 0;
+    int bad = -1;
+    for (int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 3; cps >= 1; --cps) {
+      budget = (int64_t)smem_sm / cps - 1024 - 256;
+      budget = std::min<int64_t>(budget, optin - 256) / 128 * 128;
+      bad = -1;
+      for (int j = 0; j < batch && bad < 0; ++j) {
+        int S = thr / bl_group(nx[j] + nu[j]);
+        while (S >= 2 && blk_region_words(nx[j], nu[j], lti, precision, S) * (int64_t)ts > budget) --S;
+        if (S < 2) bad = j;
+        grp[j] = S;
+      }
+      if (bad < 0 || sc.ctas_per_sm > 0) break;
+    }
+    if (bad >= 0) {
+      char b[200];
+      snprintf(b, sizeof b, "instance %d (nx %d, nu %d) does not fit the blocked schedule in %lld bytes",
+               bad, nx[bad], nu[bad], (long long)budget);
+      why = b;
+      return PIMPC_EINVAL;
+    }
+    int64_t words_max = 4, total_sub = 0;
+    for (int j = 0; j < batch; ++j) {
+      const int n = nx[j] + nu[j];
+      const int S = grp[j];
+      words_max = std::max<int64_t>(words_max, blk_region_words(nx[j], nu[j], lti, precision, S));
+      W[j] = bl_block_words(nx[j], nu[j], (int)ts);
+      blk[j] = tot_blk;
+      tot_blk += ((int64_t)blocks_per_instance(lti, N[j]) * W[j] + 31) / 32 * 32;
+      Ni[j] = tot_Ni;
+      tot_Ni += ((int64_t)N[j] * bl_rec(n) + 31) / 32 * 32;
+      total_sub += (N[j] + S - 2) / (S - 1);
+    }
+    P.threads = thr;
+    s->smem_admm = (size_t)words_max * ts;
+    e = blk_configure(precision, s->smem_admm, &bps);
+    if (e == cudaSuccess && bps >= 1) {
+      const int64_t max_grid = (int64_t)bps * nsm;
+      // Sub-chunks per item: enough items for about 4 per CTA, at most 16 sub-chunks per item.
+      int64_t m = sc.item_scale > 0 ? sc.item_scale : total_sub / (4 * max_grid);
+      m = std::max<int64_t>(1, std::min<int64_t>(sc.item_scale > 0 ? 64 : 16, m));
+      for (int oi = 0; oi < batch; ++oi) {
+        const int j = order[oi];
+        const int P1 = grp[j] - 1;
+        int is = (int)(P1 * m);
+        if (lti) is = std::max(is, std::min(N[j], (256 + P1 - 1) / P1 * P1));
+        for (int a0 = 0; a0 < N[j]; a0 += is) {
+          item_inst.push_back(j);
+          item_a.push_back(a0);
+          item_b.push_back(std::min(N[j], a0 + is));
+          nitems_inst[j] += 1;
+        }
+      }
+    }
   } else if (tiled == 2) {
     // Shared-memory budget of one CTA, and per instance the widest tile that fits it.
     const int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 2;
@@ -367,7 +428,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   int64_t *d_blk = nullptr, *d_Ni = nullptr;
-  int *d_W = nullptr, *d_tw = nullptr;
+  int *d_W = nullptr, *d_tw = nullptr, *d_grp = nullptr;
   chk(lalloc(s, &s->blk_T, ts * tot_blk));
   for (int b = 0; b < 3; ++b) chk(lalloc(s, &s->it[b], ts * tot_Ni));
   chk(lalloc(s, &s->item_inst, sizeof(int) * nitems));
@@ -379,6 +440,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(lalloc(s, &d_Ni, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_W, sizeof(int) * batch));
   chk(lalloc(s, &d_tw, sizeof(int) * batch));
+  chk(lalloc(s, &d_grp, sizeof(int) * batch));
   if (e != cudaSuccess) {
     why = std::string("device allocation failed: ") + cudaGetErrorString(e);
     const bool oom = e == cudaErrorMemoryAllocation;
@@ -394,6 +456,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(cudaMemcpy(d_Ni, Ni.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_W, W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_tw, tw.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(d_grp, grp.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemset(s->blk_T, 0, ts * tot_blk));
   for (int b = 0; b < 3; ++b) chk(cudaMemset(s->it[b], 0, ts * tot_Ni));
   chk(cudaMemset(s->base, 0, sizeof(int) * batch));
@@ -412,6 +475,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   s->nitems = nitems;
   s->grid_admm = grid;
   P.grid = grid;
+  P.grp = d_grp;
   s->plan = P;
   s->sched = sc;
   s->L.tiled = tiled;
@@ -461,6 +525,7 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   if (s->sched.family == 3 && s->coef_len < s->max_iters + 1)
     return fail(s, PIMPC_ESTATE, "momentum table shorter than max_iters");
   PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st)
+                 : s->tiled == 3 ? launch_blk(a, s->prec, s->smem_admm, st)
                  : s->sched.family == 3 ? launch_resident(a, s->prec, s->res_plan, s->smem_admm, st)
                  : s->sched.family == 4 ? launch_gemm(a, s->prec, s->gemm_plan, st)
                                         : launch_admm(a, s->prec, st),

@@ -117,10 +117,14 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   chol_inverse(S, X, n, ld, lane, a.err);
 
   const int W = a.L.W[j];
-  const bool tiled = a.L.tiled != 0;
-  const int ldg = tiled ? n : odd_ld(n);
-  const int oE = nx * ldg, oH = oE + nx;
-  const int oM = oH + (tiled ? packed_size(n) : wrapped_size(n));
+  const int lay = a.L.tiled;
+  const bool packed = lay == 1 || lay == 2;  // symmetric matrices packed lower
+  const bool blocked = lay == 3;
+  const int ts = (int)sizeof(T);
+  const int ldg = blocked ? bl_ldg(n, ts) : (packed ? n : odd_ld(n));
+  const int oE = nx * ldg;
+  const int oH = blocked ? bl_oH(nx, nu, ts) : oE + nx;
+  const int oM = blocked ? bl_oM(nx, nu, ts) : oH + (packed ? packed_size(n) : wrapped_size(n));
   // Element e of this block: tiled stage-varying data interleaves 32 stages element-major;
   // halo tiles interleave tw slots and hold the stage up to three times (its own slot and the
   // halo slots of the neighbouring tiles); everything else is a plain block.
@@ -135,7 +139,7 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     const int m = halo_copies(tw, N, kb, tt, ss);
     for (int q = 0; q < m; ++q) bases[1 + q] = blk + a.L.blk[j] + (int64_t)tt[q] * W + ss[q];
     nb = 1 + m;
-  } else if (tiled && !lti) {
+  } else if (lay == 1 && !lti) {
     bases[0] = blk + a.L.blk[j] + (int64_t)(kb >> 5) * 32 * W + (kb & 31);
     es = 32;
   } else {
@@ -145,10 +149,21 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   auto put = [&](int e, double v) {
     for (int q = 0; q < nb; ++q) bases[q][(int64_t)e * es] = (T)v;
   };
-  // Symmetric matrices: packed lower row-major (one-thread-per-stage kernel) or wrapped
-  // diagonals, row d holding S[c][(c + d) mod m] (lane-group kernel).
+  // Symmetric matrices: packed lower row-major (one-thread-per-stage kernels) or wrapped
+  // diagonals, row d holding S[c][(c + d) mod m] (lane-group kernels); H of the blocked layout
+  // as wrapped 4 x 4 block diagonals (slot w is element (a, b) of block (d, I), see
+  // bl_sym_index).
+  auto put_sym_blocks = [&](int o, int m, const double *Xs, int ldx) {
+    const int nbm = bl_nb(m), Dm = bl_diags(nbm);
+    for (int w = lane; w < 16 * nbm * Dm; w += 32) {
+      const int b = w & 3, q = w >> 2;
+      const int I = q % nbm, d = (q / nbm) % Dm, a4 = q / (nbm * Dm);
+      const int r = 4 * I + a4, c = 4 * ((I + d) % nbm) + b;
+      put(o + w, (r < m && c < m) ? Xs[r * ldx + c] : 0.0);
+    }
+  };
   auto put_sym = [&](int o, int m, const double *Xs, int ldx) {
-    if (tiled) {
+    if (packed) {
       for (int i = 0; i < m; ++i)
         for (int c = lane; c <= i; c += 32) put(o + i * (i + 1) / 2 + c, Xs[i * ldx + c]);
     } else {
@@ -157,7 +172,8 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
         for (int c = lane; c < m; c += 32) put(o + d * m + c, Xs[c * ldx + (c + d) % m]);
     }
   };
-  put_sym(oH, n, X, ld);
+  if (blocked) put_sym_blocks(oH, n, X, ld);
+  else put_sym(oH, n, X, ld);
   __syncwarp();
 
   // Own-stage G_k, e_k and M_k = (B_k^T B_k + I + Wdu/rho)^{-1}.
@@ -168,9 +184,13 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     G[w] = g;
     put(r * ldg + c, g);
   }
-  if (ldg > n)
-    for (int r = lane; r < nx; r += 32) put(r * ldg + n, 0.0);
+  for (int w = lane; w < nx * (ldg - n); w += 32) {  // row padding
+    const int r = w / (ldg - n);
+    put(r * ldg + n + (w - r * (ldg - n)), 0.0);
+  }
   for (int r = lane; r < nx; r += 32) put(oE + r, e ? e[(size_t)kS * nx + r] : 0.0);
+  if (blocked)
+    for (int r = nx + lane; r < bl_pad4(nx); r += 32) put(oE + r, 0.0);
   __syncwarp();
   const double *rdu = a.rdu ? a.rdu + a.L.off_n[j] + nx : nullptr;
   for (int i = 0; i < nu; ++i)
@@ -182,7 +202,7 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     }
   chol_inverse(S, X, nu, nu, lane, a.err);
   put_sym(oM, nu, X, nu);
-  if (!tiled) {  // padding of a plain block
+  if (!packed) {  // padding of a plain or blocked block
     const int end = oM + wrapped_size(nu);
     for (int w = end + lane; w < W; w += 32) put(w, 0.0);
   }

@@ -33,6 +33,7 @@ struct AdmmLaunch {
   int *ndone, *stop;
   double *u_out, *x_out;
   const double *coef_tab;
+  const int *grp;   // blocked kernel: lane groups per sub-chunk of each instance
   int warm;
   // launch shape and shared-memory plan (elements of the iteration type)
   int grid, threads;
@@ -67,14 +68,23 @@ int gemm_plan(int max_n, int max_nx, int max_nu, int precision, size_t budget, i
 cudaError_t gemm_configure(int precision, size_t smem, int *blocks_per_sm);
 cudaError_t launch_gemm(const AdmmLaunch &s, int precision, const int *plan, cudaStream_t stream);
 
+// Lane groups owning 4-column blocks on blocked stage blocks (tiled == 3).
+int blk_threads();
+// Shared-memory elements of a sub-chunk of S lane groups (S - 1 stages and the next stage).
+int64_t blk_region_words(int nx, int nu, int lti, int precision, int S);
+cudaError_t blk_configure(int precision, size_t smem, int *blocks_per_sm);
+cudaError_t launch_blk(const AdmmLaunch &a, int precision, size_t smem, cudaStream_t stream);
+
 // Schedule of the batched solve: which kernel family and how its work is cut.
 struct Schedule {
   int family = -1;       // 0: lane groups on plain stage blocks; 2: one thread per stage on halo
                          // tiles (stage-varying FP32 only); 3: every instance resident in the
                          // shared memory of one CTA or a cluster (item_scale = CTAs per
                          // instance, 0: the fewest that fit); 4: stage-invariant instances as
-                         // dense contractions over blocks of stages; -1: the default
-  int ctas_per_sm = 0;   // halo tiles: CTAs per SM the shared-memory budget is sized for (0: 2)
+                         // dense contractions over blocks of stages; 5: lane groups owning
+                         // 4-column blocks on blocked stage blocks; -1: the default
+  int ctas_per_sm = 0;   // halo tiles and blocked lane groups: CTAs per SM the shared-memory
+                         // budget is sized for (0: 2 for halo tiles, 3 for blocked lane groups)
   int item_scale = 0;    // lane groups: sub-chunks per item (0: automatic);
                          // halo tiles: at most this many tiles per item (0: 4)
 };

@@ -38,12 +38,14 @@ struct Args {
   int *ndone, *stop;
   int capI;
   const double *coef_tab;  // momentum factor of the m-th consecutive momentum step (resident)
+  const int *grp;          // blocked kernel: lane groups per sub-chunk of each instance
 };
 
 // Iterate element (vector b in {z, v, theta, beta, lambda}, component c) of stage k (its own
 // copy). Plain layout: stage-major with stride n5p. Tiled layout: tiles of 32 stages,
 // element-major inside a tile (one 128-byte line per element for 32 stages in FP32). Halo
-// tiles: tw slots per tile (see pimpc_internal.cuh).
+// tiles: tw slots per tile (see pimpc_internal.cuh). Blocked layout: stage-major, every vector
+// padded to a multiple of 4 (n5p is not used).
 __host__ __device__ inline int64_t iter_index(int tiled, int tw, int n, int n5p, int k, int b,
                                               int c) {
   if (tiled == 1) return (int64_t)(k >> 5) * (32 * 5 * n) + (int64_t)(b * n + c) * 32 + (k & 31);
@@ -52,6 +54,7 @@ __host__ __device__ inline int64_t iter_index(int tiled, int tw, int n, int n5p,
     halo_slot(tw, k, t, s);
     return (int64_t)t * tile_iter_words(tw, n) + (int64_t)(b * n + c) * tw + s;
   }
+  if (tiled == 3) return (int64_t)k * bl_rec(n) + b * bl_pad4(n) + c;
   return (int64_t)k * n5p + b * n + c;
 }
 
@@ -262,6 +265,7 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.ndone = s.ndone; a.stop = s.stop;
   a.capI = 0;
   a.coef_tab = s.coef_tab;
+  a.grp = s.grp;
   return a;
 }
 

@@ -11,6 +11,7 @@
 // instance has N blocks at blk[j] + k W, an LTI instance two (H_k for k < N-1, then H_{N-1}).
 // Tiled layout (one-thread-per-stage kernel of pimpc_solve_static): see admm_tps.cu.
 // Halo-tile layout (tiled == 2, stage-varying instances, one thread per stage): see below.
+// Blocked layout (tiled == 3, lanes owning 4-column blocks): see below.
 //
 // Iterates (T): three rotating buffers it[0..2]; stage k of instance j holds [z | v | theta | beta |
 // lambda] (5 n values, z = z_{k+1}, padded to a 16-byte multiple n5p) at Ni[j] + n5p k. base[j]
@@ -31,7 +32,8 @@ constexpr int kMaxNLti = 64;
 struct Layout {
   int batch;
   int lti;
-  int tiled;                       // 0: plain stage-major; 1: 32-stage tiles; 2: halo tiles
+  int tiled;                       // 0: plain stage-major; 1: 32-stage tiles; 2: halo tiles;
+                                   // 3: blocked stage-major
   const int *tw;                   // halo tiles: slots per tile (tiled == 2), else null
   const int *nx, *nu, *N;          // [batch]
   const int64_t *off_nx, *off_nu, *off_n;   // per-instance vector offsets
@@ -103,6 +105,44 @@ __host__ __device__ inline int halo_copies(int tw, int N, int k, int *tt, int *s
   if (s == 1 && t >= 1) { tt[m] = t - 1; ss[m] = tw - 1; ++m; }
   return m;
 }
+
+// Blocked layout (tiled == 3). Stage-major like the plain layout, but built for lanes that own
+// 4-column blocks (16-byte vector accesses in FP32):
+//   [ G_k : nx rows of stride bl_ldg(n) ][ e_k : nx, padded to 4 ][ H_k as wrapped 4 x 4 block
+//   diagonals ][ M_k as (scalar) wrapped diagonals, padded to 4 ]
+// H_k (n x n, zero-padded to 4 nb, nb = ceil(n / 4)) is cut into 4 x 4 blocks S_{I,J}; for
+// d = 0 .. nb/2 the block S_{I,(I+d) mod nb} is stored for every block row I (blocks d and
+// nb - d are transposes of each other, so this holds every block once, those with d = nb/2 of an
+// even nb twice). Row a of block (d, I) sits at ((a D + d) nb + I) * 4 (D = nb/2 + 1): lanes
+// reading row a of consecutive blocks read consecutive 16-byte words. The G stride makes the
+// rows r, r+1, .. r+7 start in distinct 16-byte bank groups. Iterates: [z | v | theta | beta |
+// lambda], each padded to 4 (record 5 * bl_pad4(n)).
+__host__ __device__ inline int bl_pad4(int m) { return (m + 3) & ~3; }
+__host__ __device__ inline int bl_nb(int m) { return (m + 3) >> 2; }
+__host__ __device__ inline int bl_diags(int nb) { return nb / 2 + 1; }
+__host__ __device__ inline int bl_ldg(int n, int tsize) {
+  const int nb = bl_nb(n);
+  return tsize == 4 ? 4 * (nb | 1) : 4 * nb + 2;
+}
+__host__ __device__ inline int bl_sym_words(int m) {
+  const int nb = bl_nb(m);
+  return 16 * nb * bl_diags(nb);
+}
+__host__ __device__ inline int bl_sym_index(int nb, int d, int I, int a, int b) {
+  return ((a * bl_diags(nb) + d) * nb + I) * 4 + b;
+}
+// Offsets inside a blocked stage block: e, H, M; and the block size W.
+__host__ __device__ inline int bl_oE(int nx, int nu, int tsize) { return nx * bl_ldg(nx + nu, tsize); }
+__host__ __device__ inline int bl_oH(int nx, int nu, int tsize) { return bl_oE(nx, nu, tsize) + bl_pad4(nx); }
+__host__ __device__ inline int bl_oM(int nx, int nu, int tsize) {
+  return bl_oH(nx, nu, tsize) + bl_sym_words(nx + nu);
+}
+__host__ __device__ inline int bl_block_words(int nx, int nu, int tsize) {
+  return bl_oM(nx, nu, tsize) + bl_pad4(wrapped_size(nu));
+}
+__host__ __device__ inline int bl_rec(int n) { return 5 * bl_pad4(n); }
+// Lanes per stage of the blocked kernel (4 columns per lane).
+__host__ __device__ inline int bl_group(int n) { return n <= 16 ? 4 : (n <= 32 ? 8 : 16); }
 
 // Per-instance solver state kept on the device between calls.
 struct InstState {

@@ -1,8 +1,9 @@
 // tune.cu -- schedules of the batched solve and the autotuner that picks one by timing.
 //
 // A schedule fixes how the persistent solve cuts its work: the kernel family (lane groups on
-// plain stage blocks, one thread per stage on halo tiles, every instance resident in one CTA or
-// a cluster, or dense contractions over blocks of stages for stage-invariant instances), the
+// plain stage blocks, lane groups owning 4-column blocks on blocked stage blocks, one thread per
+// stage on halo tiles, every instance resident in one CTA or a cluster, or dense contractions
+// over blocks of stages for stage-invariant instances), the
 // shared-memory budget of a CTA (CTAs per SM) and the item size. Changing the schedule changes the data layout, so the stage cache is rebuilt and the
 // iterates restart from zero at the next solve. The autotuner times a fixed number of
 // iterations of every candidate on the solver's own batch with CUDA events and keeps the
@@ -60,6 +61,12 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
     Schedule c;
     c.family = 0;
     c.item_scale = m;
+    cands.push_back(c);
+  }
+  for (int cps : {2, 3, 4}) {
+    Schedule c;
+    c.family = 5;  // blocked lane groups, shared memory sized for cps CTAs per SM
+    c.ctas_per_sm = cps;
     cands.push_back(c);
   }
   {

@@ -234,7 +234,7 @@ def pimpc_solve_static(nx, nu, N, precision, A, B, e, q, r, xmin, xmax, umin, um
                                            float(eta), *p[11:], st))
 
 
-FAMILY_LANES, FAMILY_TILES, FAMILY_RESIDENT, FAMILY_CONTRACTION = 0, 2, 3, 4
+FAMILY_LANES, FAMILY_TILES, FAMILY_RESIDENT, FAMILY_CONTRACTION, FAMILY_BLOCKED = 0, 2, 3, 4, 5
 
 
 def pimpc_set_graph(h, enable):

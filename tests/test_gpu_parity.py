@@ -260,13 +260,13 @@ def test_device_memory_calls_match_host_calls():
 POLISH_DIMS = [(4, 2, 37), (14, 2, 19), (12, 4, 33), (6, 2, 1), (9, 9, 17), (24, 8, 45)]
 
 
-@pytest.mark.parametrize("family", [pimpc.FAMILY_LANES, pimpc.FAMILY_TILES])
+@pytest.mark.parametrize("family", [pimpc.FAMILY_LANES, pimpc.FAMILY_TILES, pimpc.FAMILY_BLOCKED])
 def test_fp64_polish_reaches_the_fp64_solution(family):
     """FP32 iterations to eps = 1e-8, then FP64 iterations to 1e-22: the result must match the
     converged FP64 oracle to 1e-9, far below what FP32 iterations alone reach (about 1e-6)."""
     insts = ragged_batch(31, dims=POLISH_DIMS)
     s = pimpc.Solver(insts, precision=pimpc.F32, eps=1e-8, max_iters=20000, accel=1)
-    if family == pimpc.FAMILY_TILES:
+    if family != pimpc.FAMILY_LANES:
         s.set_schedule(family)
     plain = s.solve()
     s.set_polish(200000, 1e-22)
