@@ -170,21 +170,32 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    src = os.path.join(HERE, "paper_2601_14414_gb300", "csrc", "admm.cu")
+# The solve kernel of each schedule family: (kernel name, source file, committed ncu summary).
+SOLVE_KERNELS = {
+    0: ("admm_kernel<float>", "admm.cu", "admm_kernel_f32_batched_512x30.md"),
+    5: ("blk_kernel<float>", "admm_blk.cu", "blk_kernel_f32_batched_512x30.md"),
+}
+
+
+def kernel_source_hash(source):
+    src = os.path.join(HERE, "paper_2601_14414_gb300", "csrc", source)
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic(profile_name):
-    """DRAM bytes per launch of the ADMM kernel from the committed ncu summary, if it was taken on
-    the current kernel source (its admm.cu hash matches); else None."""
+def profiled_traffic(family):
+    """DRAM bytes per algorithmic byte of the solve kernel from the committed ncu summary (a
+    smaller case of the same workload; traffic grows in proportion to the stage-iterations), if
+    it was taken on the current kernel source (the summary's source hash matches); else None."""
+    if family not in SOLVE_KERNELS:
+        return None
+    _, source, profile_name = SOLVE_KERNELS[family]
     path = os.path.join(HERE, "profiles", profile_name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m_hash = re.search(r"admm\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
-    m_traffic = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+-]+)", text)
-    if not m_hash or not m_traffic or m_hash.group(1) != kernel_source_hash():
+    m_hash = re.search(re.escape(source) + r" sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_traffic = re.search(r"traffic_per_algorithmic_byte:\s*([0-9.eE+-]+)", text)
+    if not m_hash or not m_traffic or m_hash.group(1) != kernel_source_hash(source):
         return None
     return float(m_traffic.group(1))
 
@@ -589,7 +600,10 @@ def run_ours(args):
     solve_s = float(np.mean(solve_ms)) / 1e3
     peak, peak_kind = load_peaks()
     achieved = alg / solve_s / 1e9
-    traffic = profiled_traffic("admm_kernel_f32_batched_512x30.md")
+    family = pimpc.pimpc_get_schedule(h)["family"]
+    ratio = profiled_traffic(family)
+    traffic = None if ratio is None else ratio * alg
+    kernel_name = SOLVE_KERNELS.get(family, ("family %d" % family,))[0]
 
     line = None
     if rank == 0:
@@ -689,7 +703,7 @@ def run_ours(args):
             breakdown_ms=dict(factorise=float(np.mean(fact_ms)), solve=float(np.mean(solve_ms))),
             roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
                           frac=achieved / peak, traffic=traffic,
-                          kernel="admm_kernel<float>", peak_kind=peak_kind,
+                          kernel=kernel_name, peak_kind=peak_kind,
                           algorithmic_bytes_per_launch=alg),
             fp64_single_instance_gpu=single,
             cpu_baseline=cpu,

@@ -130,7 +130,10 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   const int batch = s->batch, lti = s->lti, precision = s->prec;
   const size_t ts = tsize(precision);
   const std::vector<int> &nx = s->nx, &nu = s->nu, &N = s->N;
-  if (sc.family < 0) sc.family = 0;  // lane groups; halo tiles are chosen explicitly or by the autotuner
+  // Default: blocked lane groups for FP32 iterations, plain lane groups for FP64 ones (the FP64
+  // pipe bounds those, and the 4-wide padding of the blocked layout adds FP64 work); the other
+  // families are chosen explicitly or by the autotuner.
+  if (sc.family < 0) sc.family = precision == PIMPC_F32 ? 5 : 0;
   if (sc.family != 0 && sc.family != 2 && sc.family != 3 && sc.family != 4 && sc.family != 5) {
     why = "schedule family must be 0, 2, 3, 4 or 5";
     return PIMPC_EINVAL;
@@ -212,22 +215,39 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     e = gemm_configure(precision, s->smem_admm, &bps);
   } else if (tiled == 3) {
     // Per instance the most lane groups (S - 1 stages and the next stage per sub-chunk) whose
-    // shared memory fits the budget of cps CTAs per SM; by default 3 CTAs per SM, or fewer when
-    // an instance needs it.
+    // shared memory fits the budget of cps CTAs per SM. By default the cps in 3, 2, 1 with the
+    // most stages in flight per SM (cps times the stage-weighted mean of S - 1) among those that
+    // fit every instance.
     const int thr = blk_threads();
+    auto fit = [&](int cps, std::vector<int> &S_of, int64_t &bud) {
+      bud = std::min<int64_t>((int64_t)smem_sm / cps - 1024 - 256, optin - 256) / 128 * 128;
+      for (int j = 0; j < batch; ++j) {
+        int S = thr / bl_group(nx[j] + nu[j]);
+        while (S >= 2 && blk_region_words(nx[j], nu[j], lti, precision, S) * (int64_t)ts > bud) --S;
+        if (S < 2) return j;
+        S_of[j] = S;
+      }
+      return -1;
+    };
     int64_t budget = 0;
     int bad = -1;
-    for (int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 3; cps >= 1; --cps) {
-      budget = (int64_t)smem_sm / cps - 1024 - 256;
-      budget = std::min<int64_t>(budget, optin - 256) / 128 * 128;
-      bad = -1;
-      for (int j = 0; j < batch && bad < 0; ++j) {
-        int S = thr / bl_group(nx[j] + nu[j]);
-        while (S >= 2 && blk_region_words(nx[j], nu[j], lti, precision, S) * (int64_t)ts > budget) --S;
-        if (S < 2) bad = j;
-        grp[j] = S;
+    if (sc.ctas_per_sm > 0) {
+      bad = fit(sc.ctas_per_sm, grp, budget);
+    } else {
+      double best = -1.0;
+      std::vector<int> S_try(batch);
+      for (int cps = 3; cps >= 1; --cps) {
+        int64_t b = 0;
+        const int r = fit(cps, S_try, b);
+        if (r >= 0) { if (best < 0.0) { bad = r; budget = b; } continue; }
+        double num = 0.0, den = 0.0;
+        for (int j = 0; j < batch; ++j) {
+          num += (double)N[j] * (S_try[j] - 1);
+          den += (double)N[j];
+        }
+        const double score = cps * num / den;
+        if (score > best) { best = score; grp = S_try; budget = b; bad = -1; }
       }
-      if (bad < 0 || sc.ctas_per_sm > 0) break;
     }
     if (bad >= 0) {
       char b[200];
@@ -253,9 +273,9 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     e = blk_configure(precision, s->smem_admm, &bps);
     if (e == cudaSuccess && bps >= 1) {
       const int64_t max_grid = (int64_t)bps * nsm;
-      // Sub-chunks per item: enough items for about 4 per CTA, at most 16 sub-chunks per item.
+      // Sub-chunks per item: enough items for about 4 per CTA, at most 64 sub-chunks per item.
       int64_t m = sc.item_scale > 0 ? sc.item_scale : total_sub / (4 * max_grid);
-      m = std::max<int64_t>(1, std::min<int64_t>(sc.item_scale > 0 ? 64 : 16, m));
+      m = std::max<int64_t>(1, std::min<int64_t>(64, m));
       for (int oi = 0; oi < batch; ++oi) {
         const int j = order[oi];
         const int P1 = grp[j] - 1;

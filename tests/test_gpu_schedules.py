@@ -81,7 +81,9 @@ def test_halo_tiles_warm_start(mode):
 
 def test_lane_group_item_sizes_agree():
     insts = ragged_batch(25)
-    base = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=120, accel=1).solve()
+    b = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=120, accel=1)
+    b.set_schedule(pimpc.FAMILY_LANES)
+    base = b.solve()
     for scale in (1, 3, 40):
         s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=120, accel=1)
         s.set_schedule(pimpc.FAMILY_LANES, 0, scale)
