@@ -23,7 +23,9 @@
 //
 // Data movement as in admm.cu: one cp.async.bulk batch per sub-chunk completing on an mbarrier
 // (stage blocks, the next stage's G and e, current and previous iterates, the halo); every wait
-// is bounded. The number of groups S of an instance is fixed on the host so that the
+// is bounded. While a sub-chunk computes, the next one of the item is prefetched into L2
+// (cp.async.bulk.prefetch.L2), so that its copies, issued once the single buffer is free, read
+// L2 rather than HBM. The number of groups S of an instance is fixed on the host so that the
 // sub-chunk's shared memory fits the budget of the requested CTAs per SM.
 #include <math.h>
 
@@ -240,6 +242,17 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         if (lti && first) bulk_load(hB, blk, (uint32_t)(2 * W * TS), &mbar);
       };
 
+      // L2 prefetch of the sub-chunk that starts at stage k0 (the same ranges as its copies):
+      // its HBM reads overlap the current sub-chunk, and its copies then read L2.
+      auto prefetch = [&](int k0) {
+        const int cnt = min(P, kb - k0);
+        const int la = (k0 + cnt < N) ? 1 : 0;
+        const uint32_t it_bytes = (uint32_t)((cnt + la) * rec * TS);
+        if (!lti) bulk_prefetch_l2(blk + (int64_t)k0 * W, (uint32_t)((cnt * W + la * oH) * TS));
+        bulk_prefetch_l2(Ic + (int64_t)k0 * rec, it_bytes);
+        if (use_prev) bulk_prefetch_l2(Ip + (int64_t)k0 * rec, it_bytes);
+      };
+
       const int nsub = (kb - ka + P - 1) / P;
       if (tid == 0) issue(ka, true);
       pend = true;
@@ -251,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           if (tid == 0) issue(k0, false);
           pend = true;
         }
+        if (tid == 0 && sc + 1 < nsub) prefetch(k0 + P);
         if (tid == 0) sArr = mbar_wait(&mbar, par, ctl) ? 1 : 0;
         __syncthreads();
         const bool arrived = sArr != 0;

@@ -162,7 +162,12 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   std::vector<int64_t> blk(batch), Ni(batch);
   int64_t tot_blk = 0, tot_Ni = 0;
   AdmmLaunch P{};
-  std::vector<int> item_inst, item_a, item_b, nitems_inst(batch, 0);
+  // Items: the coarse ones, then (lane-group families, stage-varying batches) the fine ones of
+  // one sub-chunk each, which the solve switches to when few instances are left.
+  std::vector<int> item_inst, item_a, item_b, nitems_inst(2 * batch, 0);
+  std::vector<int> fine_len(batch, 0);  // stages per fine item (0: no fine items)
+  const int fine_sub = 1;                 // sub-chunks per fine item
+  const int fine_switch = 1;              // fine items below this many coarse items per CTA
   // Instance order: largest streamed volume first.
   std::vector<int> order(batch);
   std::iota(order.begin(), order.end(), 0);
@@ -281,6 +286,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
         const int P1 = grp[j] - 1;
         int is = (int)(P1 * m);
         if (lti) is = std::max(is, std::min(N[j], (256 + P1 - 1) / P1 * P1));
+        if (!lti && m > fine_sub) fine_len[j] = P1 * fine_sub;
         for (int a0 = 0; a0 < N[j]; a0 += is) {
           item_inst.push_back(j);
           item_a.push_back(a0);
@@ -424,6 +430,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
         const int S = threads / admm_group_size(n);
         int is = (int)(S * m);
         if (lti) is = std::max(is, std::min(N[j], (256 + S - 1) / S * S));
+        if (!lti && m > fine_sub) fine_len[j] = S * fine_sub;
         for (int a0 = 0; a0 < N[j]; a0 += is) {
           item_inst.push_back(j);
           item_a.push_back(a0);
@@ -440,6 +447,17 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   }
   const int nitems = (int)item_inst.size();
   const int grid = (int)std::min<int64_t>((int64_t)bps * nsm, nitems);
+  for (int oi = 0; oi < batch; ++oi) {
+    const int j = order[oi];
+    if (fine_len[j] <= 0) continue;
+    for (int a0 = 0; a0 < N[j]; a0 += fine_len[j]) {
+      item_inst.push_back(j);
+      item_a.push_back(a0);
+      item_b.push_back(std::min(N[j], a0 + fine_len[j]));
+      nitems_inst[batch + j] += 1;
+    }
+  }
+  const int nall = (int)item_inst.size();
 
   // (Re)allocate and upload what depends on the schedule.
   cudaDeviceSynchronize();
@@ -451,11 +469,11 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   int *d_W = nullptr, *d_tw = nullptr, *d_grp = nullptr;
   chk(lalloc(s, &s->blk_T, ts * tot_blk));
   for (int b = 0; b < 3; ++b) chk(lalloc(s, &s->it[b], ts * tot_Ni));
-  chk(lalloc(s, &s->item_inst, sizeof(int) * nitems));
-  chk(lalloc(s, &s->item_a, sizeof(int) * nitems));
-  chk(lalloc(s, &s->item_b, sizeof(int) * nitems));
-  chk(lalloc(s, &s->list0, sizeof(int) * nitems));
-  chk(lalloc(s, &s->list1, sizeof(int) * nitems));
+  chk(lalloc(s, &s->item_inst, sizeof(int) * nall));
+  chk(lalloc(s, &s->item_a, sizeof(int) * nall));
+  chk(lalloc(s, &s->item_b, sizeof(int) * nall));
+  chk(lalloc(s, &s->list0, sizeof(int) * nall));
+  chk(lalloc(s, &s->list1, sizeof(int) * nall));
   chk(lalloc(s, &d_blk, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_Ni, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_W, sizeof(int) * batch));
@@ -468,10 +486,10 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     (void)cudaGetLastError();
     return oom ? PIMPC_ENOMEM : PIMPC_ECUDA;
   }
-  chk(cudaMemcpy(s->item_inst, item_inst.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(s->item_a, item_a.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(s->item_b, item_b.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(s->nitems_inst, nitems_inst.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_inst, item_inst.data(), sizeof(int) * nall, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_a, item_a.data(), sizeof(int) * nall, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_b, item_b.data(), sizeof(int) * nall, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->nitems_inst, nitems_inst.data(), sizeof(int) * 2 * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_blk, blk.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_Ni, Ni.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_W, W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
@@ -496,6 +514,9 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   s->grid_admm = grid;
   P.grid = grid;
   P.grp = d_grp;
+  P.nfine_base = nitems;
+  P.nfine = nall - nitems;
+  P.fine_switch = fine_switch;
   s->plan = P;
   s->sched = sc;
   s->L.tiled = tiled;
@@ -806,7 +827,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(dalloc(s, &s->cacc, sizeof(double) * batch));
   chk(dalloc(s, &s->ndone, sizeof(int) * batch));
   chk(dalloc(s, &s->stop, sizeof(int) * batch));
-  chk(dalloc(s, &s->nitems_inst, sizeof(int) * batch));
+  chk(dalloc(s, &s->nitems_inst, sizeof(int) * 2 * batch));
   chk(dalloc(s, &s->ctl, sizeof(Ctl)));
   chk(dalloc(s, &s->binst, sizeof(int) * s->nblocks));
   chk(dalloc(s, &s->ferr, sizeof(int) * 4));

@@ -24,6 +24,9 @@ struct AdmmLaunch {
   // work items
   const int *item_inst, *item_a, *item_b, *nitems_inst;
   int nitems;
+  // fine items (one sub-chunk each) after the nitems coarse ones: nfine of them from index
+  // nfine_base; nitems_inst holds the coarse then the fine per-instance counts (0: none)
+  int nfine_base, nfine, fine_switch;
   int *list0, *list1;
   Ctl *ctl;
   // per-instance state

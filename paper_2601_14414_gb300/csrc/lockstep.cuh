@@ -29,7 +29,9 @@ struct Args {
   int mask_len;
   const int *item_inst, *item_a, *item_b;
   int nitems;
-  const int *nitems_inst;
+  const int *nitems_inst;   // [batch] coarse counts, then [batch] fine counts
+  int nfine_base, nfine;    // fine items: nfine of them from nfine_base (0: none)
+  int fine_switch;          // switch to them below fine_switch x grid active coarse items
   int *list[2];
   Ctl *ctl;
   int *base;
@@ -98,7 +100,8 @@ __device__ inline void finish_item(const Args<T> &a, int j, int it, double part)
   atomicAdd(&a.cacc[j], part);
   __threadfence();
   const int done = atomicAdd(&a.ndone[j], 1);
-  if (done != a.nitems_inst[j] - 1) return;
+  const int fine = *(volatile int *)&a.ctl->fine;
+  if (done != a.nitems_inst[j + (fine ? a.L.batch : 0)] - 1) return;
   __threadfence();
   const double s = __longlong_as_double((long long)atomicExch((unsigned long long *)&a.cacc[j], 0ull));
   a.ndone[j] = 0;
@@ -139,20 +142,27 @@ __device__ inline void finish_item(const Args<T> &a, int j, int it, double part)
   }
 }
 
-// After the iteration barrier: drop the items of stopped instances from the active list.
-// Returns false if a barrier failed. Uniform control flow across the grid.
+// After the iteration barrier: drop the items of stopped instances from the active list. When
+// the active coarse items no longer cover the grid several times over (few instances left,
+// each item run by one CTA one sub-chunk after the other, the last items of an iteration
+// leaving most CTAs idle), the list is rebuilt from the fine items of the active instances
+// instead, so that their sub-chunks spread over the CTAs. Returns false if a barrier
+// failed. Uniform control flow across the grid (every CTA reads the same nact, stopped, fine).
 template <typename T>
 __device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk) {
   Ctl *ctl = a.ctl;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const unsigned nblocks = gridDim.x;
-  if (!*(volatile int *)&ctl->stopped) return true;
+  const bool go_fine =
+      a.nfine > 0 && !*(volatile int *)&ctl->fine && nact < a.fine_switch * (int)nblocks;
+  if (!*(volatile int *)&ctl->stopped && !go_fine) return true;
   const int src = cl, dst = cl ^ 1;
-  for (int b0 = blockIdx.x * nthreads; b0 < nact; b0 += nblocks * nthreads) {
+  const int total = go_fine ? a.nfine : nact;
+  for (int b0 = blockIdx.x * nthreads; b0 < total; b0 += nblocks * nthreads) {
     const int qi = b0 + tid;
     int keep = 0, item = 0;
-    if (qi < nact) {
-      item = a.list[src][qi];
+    if (qi < total) {
+      item = go_fine ? a.nfine_base + qi : a.list[src][qi];
       keep = *(volatile int *)&a.stop[a.item_inst[item]] == 0;
     }
     const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -166,6 +176,7 @@ __device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk) {
   if (blockIdx.x == 0 && tid == 0) {
     ctl->nlist[src] = 0;
     ctl->stopped = 0;
+    if (go_fine) ctl->fine = 1;
   }
   return grid_sync(ctl, nblocks, sOk);
 }
@@ -258,6 +269,7 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.mask = s.mask; a.mask_len = s.mask_len;
   a.item_inst = s.item_inst; a.item_a = s.item_a; a.item_b = s.item_b;
   a.nitems = s.nitems; a.nitems_inst = s.nitems_inst;
+  a.nfine_base = s.nfine_base; a.nfine = s.nfine; a.fine_switch = s.fine_switch;
   a.list[0] = s.list0; a.list[1] = s.list1;
   a.ctl = s.ctl;
   a.base = s.base; a.st = s.st;

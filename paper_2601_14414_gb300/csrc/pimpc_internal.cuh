@@ -54,7 +54,8 @@ struct Ctl {
   int stopped;           // some instance stopped in this iteration
   int err;               // nonzero: a bounded wait timed out
   int nlist[2];          // lengths of the two active-item lists
-  int pad[7];
+  int fine;              // the active list holds the fine items (one sub-chunk each)
+  int pad[6];
 };
 
 __host__ __device__ inline int packed_size(int n) { return n * (n + 1) / 2; }
