@@ -76,9 +76,10 @@ __device__ __forceinline__ V4<T> zero4() {
 // Shared-memory regions of a sub-chunk with S groups (elements of T): LTV stage blocks (S - 1
 // blocks and the next stage's G and e), current and previous iterates (S records each), the
 // halo (H_{a-1}, or both blocks of a stage-invariant instance), the halo iterates, per-group
-// scratch (5 vectors) and the xbar rows (double-buffered, S rows each).
+// scratch (5 vectors), the xbar rows (double-buffered, S rows each) and the instance's Qbar
+// diagonal and bounds.
 struct Regions {
-  int rawI, capI, haloB, haloI, scr, X, total;
+  int rawI, capI, haloB, haloI, scr, X, prm, total;
 };
 
 __host__ __device__ inline Regions regions(int nx, int nu, int lti, int tsize, int S) {
@@ -91,7 +92,8 @@ __host__ __device__ inline Regions regions(int nx, int nu, int lti, int tsize, i
   r.haloI = r.haloB + bl_pad4(lti ? 2 * W : bl_sym_words(n));
   r.scr = r.haloI + 2 * rec;
   r.X = r.scr + S * 5 * nP;
-  r.total = r.X + 2 * S * nP;
+  r.prm = r.X + 2 * S * nP;  // the instance's Qbar diagonal and bounds (3 vectors)
+  r.total = r.prm + 3 * nP;
   return r;
 }
 
@@ -212,7 +214,16 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       const T *rIc = sm + R.rawI, *rIp = sm + R.rawI + R.capI;
       T *hB = sm + R.haloB, *hI = sm + R.haloI;
       const T *ltiB = hB;  // stage-invariant: block 0 (H_k, k < N-1) then block 1 (H_{N-1})
+      T *sQd = sm + R.prm, *sLo = sQd + nP, *sHi = sLo + nP;
       T cacc = (T)0;
+      // Qbar diagonal and bounds of the instance into shared memory (read before the first
+      // copy wait's barrier; the previous item's last use ended at its final barrier).
+      for (int c = tid; c < nP; c += kThreads) {
+        const bool in = c < n;
+        sQd[c] = in ? qd[c] : (T)0;
+        sLo[c] = in ? lo[c] : (T)0;
+        sHi[c] = in ? hi[c] : (T)0;
+      }
 
       // Copies of the sub-chunk that starts at stage k0 (thread 0 issues).
       auto issue = [&](int k0, bool first) {
@@ -285,7 +296,13 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
 
         // ---- phase 1: hats, y and w; q and t in one pass over G_k; du = M t ----
         V4<T> zh = zero4<T>(), vh = zero4<T>(), th = zero4<T>(), bh = zero4<T>(), lh = zero4<T>();
-        V4<T> e4 = zero4<T>(), y4 = zero4<T>(), w4 = zero4<T>();
+        V4<T> e4 = zero4<T>(), y4 = zero4<T>(), w4 = zero4<T>(), rf4 = zero4<T>();
+        if (ref && stage && own) {  // the reference of stage k, needed in phase 2
+          const T *rk = ref + (int64_t)k * refstride;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (c0 + i < n) rf4.v[i] = rk[c0 + i];
+        }
         if ((stage || look) && own) {
           zh = hat4(hc + c0, hp + c0, use_prev, f);
           vh = hat4(hc + nP + c0, hp + nP + c0, use_prev, f);
@@ -350,33 +367,24 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         if (stage && own) {
           V4<T> qn = zero4<T>();
           if (k + 1 < N) qn = ld4(scr + 5 * nP + 2 * nP + c0);  // the next group's q
+          const V4<T> qd4 = ld4(sQd + c0);
+          // h is zero beyond n, where qd, the hats, q and the reference are zero
           V4<T> h;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int c = c0 + i;
-            T v = (T)0;
-            if (c < n) {
-              const T rf = ref ? ref[(int64_t)k * refstride + c] : (T)0;
-              v = qd[c] * rf + rho * (zh.v[i] - th.v[i] + qn.v[i]);
-            }
-            h.v[i] = v;
-          }
+          for (int i = 0; i < 4; ++i) h.v[i] = qd4.v[i] * rf4.v[i] + rho * (zh.v[i] - th.v[i] + qn.v[i]);
           st4(sY + c0, h);
         }
         if (hgrp && own) {  // h_{a-1} from the halo hats and q_a (group 0)
           const V4<T> zm = hat4(hI + c0, hI + rec + c0, use_prev, f);
           const V4<T> tm = hat4(hI + 2 * nP + c0, hI + rec + 2 * nP + c0, use_prev, f);
           const V4<T> qa = ld4(sm + R.scr + 2 * nP + c0);
+          const V4<T> qd4 = ld4(sQd + c0);
           V4<T> h;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int c = c0 + i;
-            T v = (T)0;
-            if (c < n) {
-              const T rf = ref ? ref[(int64_t)(ka - 1) * refstride + c] : (T)0;
-              v = qd[c] * rf + rho * (zm.v[i] - tm.v[i] + qa.v[i]);
-            }
-            h.v[i] = v;
+            const T rf = (ref && c < n) ? ref[(int64_t)(ka - 1) * refstride + c] : (T)0;
+            h.v[i] = qd4.v[i] * rf + rho * (zm.v[i] - tm.v[i] + qa.v[i]);
           }
           st4(sY + c0, h);
         }
@@ -420,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           const T *xk = Xc + grp * nP, *xk1 = Xc + (grp + 1) * nP;
           const V4<T> x1 = ld4(xk1 + c0), x0 = ld4(xk + c0), du4 = ld4(sDU + c0);
           const V4<T> ax4 = ld4(sY + c0), bd4 = ld4(sW + c0);
+          const V4<T> lo4 = ld4(sLo + c0), hi4 = ld4(sHi + c0);
           V4<T> oz, ov, ot, ob, ol;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -432,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
               const T xn = x1.v[i];
               const T gam = bd + bh.v[i] - ax - ee + lh.v[i];
               const T w = ((T)2 * (xn + th.v[i] + ax + ee - lh.v[i]) + gam) / (T)3;
-              const T z = clampv(w, lo[c], hi[c]);
+              const T z = clampv(w, lo4.v[i], hi4.v[i]);
               const T v = (T)0.5 * (z + gam);
               const T tt = th.v[i] + xn - z;
               const T be = bh.v[i] + bd - v;
