@@ -179,7 +179,11 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
           if (!lti) bytes += (uint32_t)(W * sizeof(T));
         }
         if (lti && first) bytes += (uint32_t)(2 * W * sizeof(T));
-        fence_proxy_async();
+        // The iterates the copies read were written through the generic proxy by other CTAs
+        // before the grid barrier: one proxy fence after that barrier, i.e. at the item's first
+        // copy, orders them before every later copy of the item. (The shared-memory buffer the
+        // copies overwrite was only read, and those reads precede the CTA barrier.)
+        if (first) fence_proxy_async();
         mbar_expect_tx(&mbar[b], bytes);
         T *rB = sm + lay.rawB + b * lay.capB;
         T *rI = sm + lay.rawI + b * 2 * lay.capI;

@@ -240,7 +240,11 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           if (!lti) bytes += (uint32_t)(symW * TS);
         }
         if (lti && first) bytes += (uint32_t)(2 * W * TS);
-        fence_proxy_async();
+        // The iterates the copies read were written through the generic proxy by other CTAs
+        // before the grid barrier: one proxy fence after that barrier, i.e. at the item's first
+        // copy, orders them before every later copy of the item. (The shared-memory buffer the
+        // copies overwrite was only read, and those reads precede the CTA barrier.)
+        if (first) fence_proxy_async();
         mbar_expect_tx(&mbar, bytes);
         if (!lti) bulk_load(rB, blk + (int64_t)k0 * W, blk_bytes, &mbar);
         bulk_load(sm + R.rawI, Ic + (int64_t)k0 * rec, it_bytes, &mbar);
