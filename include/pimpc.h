@@ -256,16 +256,23 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
  * Schedules of the batched solve (no counterpart in the paper: how the GPU cuts the work of
  * Algorithm 1 across its SMs; the arithmetic of an iteration is the same under every schedule,
  * up to the order of the sums in c).
- *   family       0: a group of lanes per stage on plain stage blocks (every precision and
- *                   instance kind; the default); 2: one thread per stage on halo tiles
- *                   (stage-varying FP32 instances only); 3: every instance resident in the
- *                   shared memory of one CTA or of a thread-block cluster for the whole solve
- *                   (no grid-wide synchronisation; for instances that fit); 4: stage-invariant
- *                   instances only, the per-stage products of blocks of stages as dense
- *                   matrix-matrix contractions; -1: the default.
- *   ctas_per_sm  families 2 and 4: CTAs per SM the shared-memory budget of a CTA is sized
- *                for (0 = 2 for family 2, 1 for family 4); ignored by families 0 and 3.
- *   item_scale   family 0: stage sub-chunks per work item (0 = automatic); family 2: at most
+ *   family       0: a group of lanes per stage on plain stage blocks, one component per lane
+ *                   (every precision and instance kind; the default for FP64 iterations);
+ *                   2: one thread per stage on halo tiles (stage-varying FP32 instances only);
+ *                   3: every instance resident in the shared memory of one CTA or of a
+ *                   thread-block cluster for the whole solve (no grid-wide synchronisation;
+ *                   for instances that fit); 4: stage-invariant instances only, the per-stage
+ *                   products of blocks of stages as dense matrix-matrix contractions; 5: a
+ *                   group of 4, 8 or 16 lanes per stage on blocked stage blocks, four
+ *                   components per lane (every precision and instance kind; the default for
+ *                   FP32 iterations); -1: the default.
+ *   ctas_per_sm  families 2, 4 and 5: CTAs per SM the shared-memory budget of a CTA is sized
+ *                for (0 = 2 for family 2, 1 for family 4; for family 5 the one of 3, 2, 1 that
+ *                fits every instance with the most stages in flight); ignored by families 0
+ *                and 3.
+ *   item_scale   families 0 and 5: stage sub-chunks per work item (0 = automatic; when the
+ *                active items no longer cover the grid the solve switches to items of one
+ *                sub-chunk for stage-varying batches); family 2: at most
  *                this many tiles per work item (0 = 4); family 3: CTAs per instance, 1, 2, 4,
  *                8 or 16 (0 = the fewest whose shared memory holds the instance, or the most
  *                that leave each CTA four stages when the batch occupies few SMs); family 4:
@@ -289,8 +296,9 @@ int pimpc_get_schedule(pimpc_solver *s, int *family, int *ctas_per_sm, int *item
  * pimpc_autotune -- times trial_iters iterations (zero start, no reference, the accel option in
  * force) of every candidate schedule on this solver's batch, with its current dynamics, weights
  * and bounds, using CUDA events on `stream`, and keeps the fastest. Candidates: family 0 with
- * item_scale 0, 2 and 8; family 3 where the instances fit; family 4 for stage-invariant
- * batches; family 2 with 1 and 2 CTAs per SM where the batch allows it. The
+ * item_scale 0, 2 and 8; family 5 with 2, 3 and 4 CTAs per SM; family 3 where the instances
+ * fit; family 4 for stage-invariant batches; family 2 with 1 and 2 CTAs per SM where the batch
+ * allows it. The
  * chosen schedule and its time (ms, the second of two trial solves) are returned through the
  * pointers (host memory, any may be NULL). The stage cache and the iterates are rebuilt as for
  * pimpc_set_schedule. Blocks the host until the trials finish.

@@ -1,6 +1,6 @@
-// admm.cu -- Algorithm 1 with a group of lanes per stage on plain stage blocks: stage-invariant
-// instances (n <= 64) and every FP64 solve. (Stage-varying FP32 instances run one thread per
-// stage on halo tiles, admm_tile.cu.)
+// admm.cu -- Algorithm 1 with a group of lanes per stage on plain stage blocks, one component per
+// lane (schedule family 0, the default for FP64 iterations; FP32 iterations default to the
+// blocked lane groups of admm_blk.cu).
 //
 // Work decomposition. The stages of every instance are cut into items of consecutive stages
 // (item = instance j, stages [a, b)). One cooperative launch runs all iterations of all

@@ -1,0 +1,145 @@
+"""The blocked stage-block layout (schedule family 5) checked on the CPU against the mathematics.
+
+The layout helpers of `csrc/pimpc_internal.cuh` are host-callable: a small C++ program compiled
+here with g++ includes that header and prints, for every matrix size m = 1..64, the block count,
+the number of stored block diagonals, the storage size and the storage index of every (block
+diagonal d, block row I, row a, column b) slot, plus the G strides and block offsets. The test
+then checks what the solve kernel relies on:
+  * the storage index is a bijection onto [0, bl_sym_words(m));
+  * storing S_{I,(I+d) mod nb} for d <= nb/2 holds every element of a symmetric m x m matrix;
+  * the per-lane product the kernel runs (per block diagonal: block (I, I+d) against h_{I+d},
+    the transpose of block (I-d, I) against h_{I-d}, the middle diagonal of an even nb once)
+    reproduces S h;
+  * G rows start 16-byte aligned and 8 consecutive rows start in 8 distinct 16-byte bank
+    groups; every offset inside a block is 16-byte aligned.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2601_14414_gb300", "csrc")
+CUDA_INC = "/usr/local/cuda/include"
+
+HARNESS = r"""
+#include <cstdio>
+#include "pimpc_internal.cuh"
+using namespace pimpc;
+int main() {
+  for (int m = 1; m <= 64; ++m) {
+    const int nb = bl_nb(m), D = bl_diags(nb);
+    std::printf("M %d %d %d %d %d %d\n", m, nb, D, bl_sym_words(m), bl_ldg(m, 4), bl_ldg(m, 8));
+    for (int d = 0; d < D; ++d)
+      for (int I = 0; I < nb; ++I)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) std::printf("S %d %d %d %d %d\n", d, I, a, b, bl_sym_index(nb, d, I, a, b));
+  }
+  for (int nx = 1; nx <= 40; ++nx)
+    for (int nu = 1; nu <= 24; ++nu)
+      for (int ts : {4, 8})
+        std::printf("B %d %d %d %d %d %d %d %d\n", nx, nu, ts, bl_oE(nx, nu, ts), bl_oH(nx, nu, ts),
+                    bl_oM(nx, nu, ts), bl_block_words(nx, nu, ts), bl_rec(nx + nu));
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def layout(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("g++ or the CUDA headers are not available")
+    d = tmp_path_factory.mktemp("bl")
+    src = d / "h.cpp"
+    exe = d / "h"
+    src.write_text(HARNESS)
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", CSRC, "-I", CUDA_INC, str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    mats, blocks, cur = {}, [], None
+    for line in out.splitlines():
+        f = line.split()
+        if f[0] == "M":
+            m, nb, D, words, ld4, ld8 = map(int, f[1:])
+            cur = dict(nb=nb, D=D, words=words, ld4=ld4, ld8=ld8, idx={})
+            mats[m] = cur
+        elif f[0] == "S":
+            dd, I, a, b, k = map(int, f[1:])
+            cur["idx"][(dd, I, a, b)] = k
+        else:
+            blocks.append(tuple(map(int, f[1:])))
+    return mats, blocks
+
+
+def test_storage_index_is_a_bijection(layout):
+    mats, _ = layout
+    for m, L in mats.items():
+        assert L["nb"] == (m + 3) // 4 and L["D"] == L["nb"] // 2 + 1
+        vals = sorted(L["idx"].values())
+        assert vals == list(range(L["words"])), m
+
+
+def stored(L, S):
+    """The storage array of the symmetric matrix S (zero-padded to 4 nb) in the blocked layout."""
+    nb, D = L["nb"], L["D"]
+    P = np.zeros((4 * nb, 4 * nb))
+    P[:S.shape[0], :S.shape[0]] = S
+    H = np.zeros(L["words"])
+    for (d, I, a, b), k in L["idx"].items():
+        H[k] = P[4 * I + a, 4 * ((I + d) % nb) + b]
+    return H
+
+
+def test_every_element_is_held_and_the_lane_products_give_S_h(layout):
+    mats, _ = layout
+    rng = np.random.default_rng(0)
+    for m, L in mats.items():
+        nb, D, idx = L["nb"], L["D"], L["idx"]
+        A = rng.standard_normal((m, m))
+        S = A + A.T
+        H = stored(L, S)
+        # every element, read back through the block diagonal that holds it (or its transpose)
+        for r in range(m):
+            for c in range(m):
+                I, a, J, b = r // 4, r % 4, c // 4, c % 4
+                d = (J - I) % nb
+                if 2 * d > nb:
+                    d, I, J, a, b = nb - d, J, I, b, a
+                assert H[idx[(d, I, a, b)]] == S[r, c]
+        # the lane products of the solve kernel
+        h = np.zeros(4 * nb)
+        h[:m] = rng.standard_normal(m)
+        y = np.zeros(4 * nb)
+        for I in range(nb):
+            for d in range(D):
+                Jp = (I + d) % nb
+                blk = np.array([[H[idx[(d, I, a, b)]] for b in range(4)] for a in range(4)])
+                y[4 * I:4 * I + 4] += blk @ h[4 * Jp:4 * Jp + 4]
+                if d > 0 and 2 * d != nb:
+                    Jm = (I - d) % nb
+                    bt = np.array([[H[idx[(d, Jm, a, b)]] for b in range(4)] for a in range(4)])
+                    y[4 * I:4 * I + 4] += bt.T @ h[4 * Jm:4 * Jm + 4]
+        np.testing.assert_allclose(y[:m], S @ h[:m], rtol=1e-12, atol=1e-12)
+        assert np.all(y[m:] == 0)
+
+
+def test_g_stride_and_offsets(layout):
+    mats, blocks = layout
+    for m, L in mats.items():
+        nb = L["nb"]
+        for ld, word in ((L["ld4"], 4), (L["ld8"], 8)):
+            assert ld >= 4 * nb and (ld * word) % 16 == 0
+            units = ld * word // 16                       # 16-byte words per row
+            starts = [(r * units) % 8 for r in range(8)]  # bank group of row r's first word
+            assert len(set(starts)) == 8, (m, word)
+    for nx, nu, ts, oE, oH, oM, W, rec in blocks:
+        n = nx + nu
+        ld = mats[n]["ld4"] if ts == 4 else mats[n]["ld8"]
+        assert oE == nx * ld and oH == oE + (nx + 3) // 4 * 4
+        assert oM == oH + mats[n]["words"] and W >= oM + nu * (nu + 1) // 2
+        for off in (oE, oH, oM, W, rec):
+            assert (off * ts) % 16 == 0, (nx, nu, ts, off)
+        assert rec == 5 * ((n + 3) // 4 * 4)
