@@ -145,7 +145,8 @@ def gpu_uuid(torch):
 
 
 # ---------------------------------------------------------------------------------------------
-# Algorithmic work (per stage-iteration; the per-unit figures stated in the design doc).
+# Algorithmic work per stage-iteration: the stage matrices (packed symmetric H and M) and the
+# iterates read and written.
 # ---------------------------------------------------------------------------------------------
 
 def matrix_words(nx, nu):
