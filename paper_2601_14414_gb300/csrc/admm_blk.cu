@@ -152,7 +152,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
-  __shared__ int sItem, sOk, sArr;
+  __shared__ int sItem, sOk;
   __shared__ double sRed[kThreads / 32];
   T *sm = reinterpret_cast<T *>(smem_raw);
   constexpr int TS = (int)sizeof(T);
@@ -280,9 +280,20 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           pend = true;
         }
         if (tid == 0 && sc + 1 < nsub) prefetch(k0 + P);
-        if (tid == 0) sArr = mbar_wait(&mbar, par, ctl) ? 1 : 0;
-        __syncthreads();
-        const bool arrived = sArr != 0;
+        // The reference of this group's stage (needed in phase 2) does not come with the copies:
+        // its loads are issued before the wait.
+        const int k = k0 + grp;
+        V4<T> rf4 = zero4<T>();
+        if (ref && grp < cnt && own) {
+          const T *rk = ref + (int64_t)k * refstride;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (c0 + i < n) rf4.v[i] = rk[c0 + i];
+        }
+        // Every thread waits on the copies itself (bounded), so no CTA barrier is needed here;
+        // a timeout seen by any thread ends the item for the whole CTA at the barrier after
+        // phase 1.
+        const bool arrived = mbar_wait(&mbar, par, ctl);
         if (arrived) {
           par ^= 1u;
           pend = false;
@@ -291,7 +302,6 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         }
         T *Xc = sm + R.X + (sc & 1) * S * nP;
         T *Xn = sm + R.X + ((sc & 1) ^ 1) * S * nP;
-        const int k = k0 + grp;
         const bool stage = arrived && grp < cnt;           // stage k of this sub-chunk
         const bool look = arrived && grp == cnt && la;     // the next stage: q only
         const bool hgrp = arrived && sc == 0 && ka > 0 && grp == S - 1;  // recomputes xbar_a
@@ -300,13 +310,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
 
         // ---- phase 1: hats, y and w; q and t in one pass over G_k; du = M t ----
         V4<T> zh = zero4<T>(), vh = zero4<T>(), th = zero4<T>(), bh = zero4<T>(), lh = zero4<T>();
-        V4<T> e4 = zero4<T>(), y4 = zero4<T>(), w4 = zero4<T>(), rf4 = zero4<T>();
-        if (ref && stage && own) {  // the reference of stage k, needed in phase 2
-          const T *rk = ref + (int64_t)k * refstride;
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (c0 + i < n) rf4.v[i] = rk[c0 + i];
-        }
+        V4<T> e4 = zero4<T>(), y4 = zero4<T>(), w4 = zero4<T>();
         if ((stage || look) && own) {
           zh = hat4(hc + c0, hp + c0, use_prev, f);
           vh = hat4(hc + nP + c0, hp + nP + c0, use_prev, f);
