@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       const T *ltiB = hB;  // stage-invariant: block 0 (H_k, k < N-1) then block 1 (H_{N-1})
       T *sQd = sm + R.prm, *sLo = sQd + nP, *sHi = sLo + nP;
       T cacc = (T)0;
-      // Qbar diagonal and bounds of the instance into shared memory (read before the first
-      // copy wait's barrier; the previous item's last use ended at its final barrier).
+      // Qbar diagonal and bounds of the instance into shared memory (first read after the
+      // barrier that ends phase 1; the previous item's last read preceded its final barrier).
       for (int c = tid; c < nP; c += kThreads) {
         const bool in = c < n;
         sQd[c] = in ? qd[c] : (T)0;
