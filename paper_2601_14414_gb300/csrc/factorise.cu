@@ -29,42 +29,55 @@ struct FactArgs {
 };
 
 // Cholesky of the m x m matrix in S (lower triangle used, leading dimension ld) in place;
-// then overwrite X (m x m, column c owned by lane c and c + 32) with S^{-1}.
-__device__ void chol_inverse(double *S, double *X, int m, int ld, int lane, int *err) {
+// then overwrite X (m x m, column c owned by lane c and c + 32) with S^{-1}. dinv (m words of
+// scratch) receives the reciprocals of the diagonal of L, taken once per column, so that the
+// column scaling and both triangular solves multiply instead of dividing.
+__device__ void chol_inverse(double *S, double *X, double *dinv, int m, int ld, int lane, int *err) {
   for (int j = 0; j < m; ++j) {
     __syncwarp();
     if (lane == 0) {
       double d = S[j * ld + j];
       for (int p = 0; p < j; ++p) d -= S[j * ld + p] * S[j * ld + p];
       if (!(d > 0.0)) { *err = 1; d = 1.0; }
-      S[j * ld + j] = sqrt(d);
+      const double l = sqrt(d);
+      S[j * ld + j] = l;
+      dinv[j] = 1.0 / l;
     }
     __syncwarp();
-    const double ljj = S[j * ld + j];
+    const double r = dinv[j];
     for (int i = j + 1 + lane; i < m; i += 32) {
       double s = S[i * ld + j];
       for (int p = 0; p < j; ++p) s -= S[i * ld + p] * S[j * ld + p];
-      S[i * ld + j] = s / ljj;
+      S[i * ld + j] = s * r;
     }
   }
   __syncwarp();
   for (int c = lane; c < m; c += 32) {
     // forward: L y = e_c  (y_i = 0 for i < c)
     for (int i = 0; i < c; ++i) X[i * ld + c] = 0.0;
-    X[c * ld + c] = 1.0 / S[c * ld + c];
+    X[c * ld + c] = dinv[c];
     for (int i = c + 1; i < m; ++i) {
       double s = 0.0;
       for (int p = c; p < i; ++p) s += S[i * ld + p] * X[p * ld + c];
-      X[i * ld + c] = -s / S[i * ld + i];
+      X[i * ld + c] = -s * dinv[i];
     }
     // backward: L^T x = y
     for (int i = m - 1; i >= 0; --i) {
       double s = X[i * ld + c];
       for (int p = i + 1; p < m; ++p) s -= S[p * ld + i] * X[p * ld + c];
-      X[i * ld + c] = s / S[i * ld + i];
+      X[i * ld + c] = s * dinv[i];
     }
   }
   __syncwarp();
+}
+
+// Row i and column c <= i of the t-th lower-triangle entry in row-major order
+// (t = i (i + 1) / 2 + c), so that a warp's lanes take consecutive entries.
+__device__ __forceinline__ void tri_index(int t, int &i, int &c) {
+  i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  c = t - i * (i + 1) / 2;
 }
 
 template <typename T>
@@ -103,18 +116,19 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     }
   }
   __syncwarp();
-  for (int i = 0; i < n; ++i)
-    for (int c = lane; c <= i; c += 32) {
-      double s = 0.0;
-      if (!terminal) {
-        for (int r = 0; r < nx; ++r) s += G[r * n + i] * G[r * n + c];
-        if (i == c && i >= nx) s += 1.0;
-      }
-      s *= rho;
-      if (i == c) s += qd[i] + rho;
-      S[i * ld + c] = s;
+  for (int t = lane; t < n * (n + 1) / 2; t += 32) {  // every lane its own (i, c), c <= i
+    int i, c;
+    tri_index(t, i, c);
+    double s = 0.0;
+    if (!terminal) {
+      for (int r = 0; r < nx; ++r) s += G[r * n + i] * G[r * n + c];
+      if (i == c && i >= nx) s += 1.0;
     }
-  chol_inverse(S, X, n, ld, lane, a.err);
+    s *= rho;
+    if (i == c) s += qd[i] + rho;
+    S[i * ld + c] = s;
+  }
+  chol_inverse(S, X, G, n, ld, lane, a.err);  // G is rebuilt below: scratch for 1/L_ii
 
   const int W = a.L.W[j];
   const int lay = a.L.tiled;
@@ -193,14 +207,16 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     for (int r = nx + lane; r < bl_pad4(nx); r += 32) put(oE + r, 0.0);
   __syncwarp();
   const double *rdu = a.rdu ? a.rdu + a.L.off_n[j] + nx : nullptr;
-  for (int i = 0; i < nu; ++i)
-    for (int c = lane; c <= i; c += 32) {
-      double s = 0.0;
-      for (int r = 0; r < nx; ++r) s += G[r * n + nx + i] * G[r * n + nx + c];
-      if (i == c) s += 1.0 + (rdu ? rdu[i] / rho : 0.0);
-      S[i * nu + c] = s;
-    }
-  chol_inverse(S, X, nu, nu, lane, a.err);
+  for (int t = lane; t < nu * (nu + 1) / 2; t += 32) {
+    int i, c;
+    tri_index(t, i, c);
+    double s = 0.0;
+    for (int r = 0; r < nx; ++r) s += G[r * n + nx + i] * G[r * n + nx + c];
+    if (i == c) s += 1.0 + (rdu ? rdu[i] / rho : 0.0);
+    S[i * nu + c] = s;
+  }
+  __syncwarp();
+  chol_inverse(S, X, G, nu, nu, lane, a.err);  // G is not read again: scratch for 1/L_ii
   put_sym(oM, nu, X, nu);
   if (!packed) {  // padding of a plain or blocked block
     const int end = oM + wrapped_size(nu);
