@@ -242,3 +242,136 @@ def test_scalar_case_by_hand():
     np.testing.assert_allclose(r2["be"], [[4 / 15, -0.2]], atol=1e-15)
     np.testing.assert_allclose(r2["la"], [[-4 / 15, 0.2]], atol=1e-15)
     assert abs(r2["c"] - 0.255) < 1e-14
+
+
+# ---------------------------------------------------------------------------------------------
+# The accelerated branch (Algorithm 1 steps 6-7) on the same scalar case, by hand.
+#
+# Steps 6-7 with the readings taken: after iteration i+1 with residual c^{i+1},
+#   * if c^{i+1} <= eta c^i: alpha_{i+1} = (1 + sqrt(1 + 4 alpha_i^2)) / 2, and every hat is
+#     hat^{i+1} = new^{i+1} + ((alpha_i - 1) / alpha_{i+1}) (new^{i+1} - new^i), the momentum
+#     taken from the previous NON-hat iterate (accelerated ADMM with restart, Goldstein et al.);
+#   * otherwise (restart): hat^{i+1} = new^{i+1} and alpha_{i+1} = 1;
+#   * in both branches c^{i+1} becomes the comparison value of the next test; alpha_0 = 1, c^0 = 1.
+# ---------------------------------------------------------------------------------------------
+
+def _scalar_inst():
+    return dict(nx=1, nu=1, N=1, lti=True, A=np.array([[0.5]]), B=np.array([[1.0]]),
+                e=np.array([0.25]), q=np.array([1.0]), r=np.array([1.0]), rdu=None,
+                xmin=np.array([-10.0]), xmax=np.array([10.0]), umin=np.array([-0.1]),
+                umax=np.array([0.1]), x0=np.array([2.0]), u_prev=None,
+                ref=np.array([1.0, 1.0]), rho=1.0)
+
+
+def _check_iterates(res, expect, atol):
+    for key, val in zip(("z", "v", "th", "be", "la"), expect):
+        np.testing.assert_allclose(res[key], [val], rtol=0, atol=atol, err_msg=key)
+
+
+PHI = (1.0 + 5.0 ** 0.5) / 2.0                       # alpha_2 = (1 + sqrt(5)) / 2
+ALPHA3 = (1.0 + (7.0 + 2.0 * 5.0 ** 0.5) ** 0.5) / 2.0  # 1 + 4 phi^2 = 7 + 2 sqrt(5)
+F3 = (PHI - 1.0) / ALPHA3                            # (alpha_2 - 1) / alpha_3 = 0.2817535...
+
+
+def test_accelerated_scalar_case_by_hand():
+    inst = _scalar_inst()
+    # Iteration 1 (the plain case above): c^1 = 1.9925 > 0.999 * c^0 = 0.999, so RESTART:
+    # hats = iteration-1 iterates, alpha_1 = 1.
+    # Iteration 2: same as the plain case, c^2 = 0.255 <= 0.999 * 1.9925: MOMENTUM with
+    # alpha_2 = phi and factor (alpha_1 - 1) / alpha_2 = 0, so the hats are still the iterates.
+    # Iteration 3, from the iteration-2 iterates z = (61/60, 1/10), v = (-13/60, -1/20),
+    # theta = (-4/15, 13/20), beta = (4/15, -1/5), lambda = (-4/15, 1/5):
+    #   du = ((-13/60 - 16/60) + (-1/20 + 1/5)) / 2 = -1/6
+    #   h = (1 + 61/60 + 16/60, 1 + 1/10 - 13/20) = (137/60, 9/20), xbar_1 = h/2 = (137/120, 9/40)
+    #   gamma = (-1/6 + 4/15 - 1 - 1/4 - 4/15, -1/6 - 1/5 + 1/5) = (-17/12, -1/6)
+    #   w = ((2 (137/120 - 4/15 + 5/4 + 4/15) - 17/12)/3, (2 (9/40 + 13/20 - 1/5) - 1/6)/3)
+    #     = (101/90, 71/180) -> z = (101/90, 1/10)
+    #   v = (-53/360, -1/30), theta = (-89/360, 31/40), beta = (89/360, -1/3), lambda = (-89/360, 1/3)
+    #   differences to the iteration-2 iterates (= its hats): dtheta = (7/360, 1/8),
+    #   dbeta = (-7/360, -2/15), dlambda = (7/360, 2/15), dz = (38/360, 0), dv = (25/360, 1/60),
+    #   d(z - v) = (13/360, -1/60), so c^3 = (2385 + 2025 + 2 * 2304 + 2 * 36) / 129600 = 101/1440.
+    r3 = oracle.solve(inst, eps=-1.0, max_iters=3, accel=1)
+    _check_iterates(r3, [(101 / 90, 0.1), (-53 / 360, -1 / 30), (-89 / 360, 0.775),
+                         (89 / 360, -1 / 3), (-89 / 360, 1 / 3)], 1e-15)
+    assert abs(r3["c"] - 101 / 1440) < 1e-15
+    # c^3 = 101/1440 <= 0.999 * 0.255: MOMENTUM, alpha_3 = (1 + sqrt(7 + 2 sqrt 5))/2 = 2.1935271,
+    # first nonzero factor f3 = (phi - 1)/alpha_3 = 0.28175353, applied to new^3 - new^2 (the
+    # differences listed above):
+    #   zhat = (101/90 + 38 f3/360, 1/10), vhat = (-53/360 + 25 f3/360, -1/30 + f3/60),
+    #   thetahat = (-89/360 + 7 f3/360, 31/40 + f3/8), betahat = (89/360 - 7 f3/360, -1/3 - 2 f3/15),
+    #   lambdahat = (-89/360 + 7 f3/360, 1/3 + 2 f3/15).
+    # Iteration 4 from these hats:
+    #   du = ((vhat - betahat)_1 + (vhat - betahat)_2)/2 = (-17 + 43 f3)/360
+    #   xbar_1 = (1 + zhat - thetahat)/2 = ((853 + 31 f3)/720, 13/80 - f3/16)
+    #   gamma = (du + betahat_1 - 5/4 + lambdahat_1, du + betahat_2 + lambdahat_2) = (du - 5/4, du)
+    #   w_1 = (2 (xbar_1 + thetahat_1 + 5/4 - lambdahat_1) + gamma_1)/3 = (2 xbar_1 + 5/4 + du)/3
+    #   w_2 = (2 (xbar_2 + thetahat_2 - lambdahat_2) + du)/3 = 0.3850 -> z_2 = 1/10
+    #   v = (z + gamma)/2, theta = thetahat + xbar - z, beta = betahat + Bbar du - v,
+    #   lambda = lambdahat + z - (1, 0) - v - (1/4, 0).
+    du4 = (-17.0 + 43.0 * F3) / 360.0
+    xb4 = ((853.0 + 31.0 * F3) / 720.0, 13.0 / 80.0 - F3 / 16.0)
+    th_h = (-89 / 360 + 7 * F3 / 360, 31 / 40 + F3 / 8)
+    be_h = (89 / 360 - 7 * F3 / 360, -1 / 3 - 2 * F3 / 15)
+    la_h = (-89 / 360 + 7 * F3 / 360, 1 / 3 + 2 * F3 / 15)
+    z4 = ((2 * xb4[0] + 1.25 + du4) / 3, 0.1)
+    v4 = ((z4[0] + du4 - 1.25) / 2, (0.1 + du4) / 2)
+    expect4 = [z4, v4,
+               (th_h[0] + xb4[0] - z4[0], th_h[1] + xb4[1] - z4[1]),
+               (be_h[0] + du4 - v4[0], be_h[1] + du4 - v4[1]),
+               (la_h[0] + z4[0] - 1.25 - v4[0], la_h[1] + z4[1] - v4[1])]
+    r4 = oracle.solve(inst, eps=-1.0, max_iters=4, accel=1)
+    np.testing.assert_allclose(r4["du"], [[du4]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r4["xb"], [xb4], rtol=0, atol=1e-15)
+    _check_iterates(r4, expect4, 1e-15)
+    # Numerically: z = (1.2100461, 0.1), v = (-0.0267611, 0.0432158), ...; c^4 = 0.0346982 <=
+    # 0.999 c^3: MOMENTUM, alpha_4 = 2.7497913, factor (alpha_3 - 1)/alpha_4 = 0.4340428 applied to
+    # new^4 - new^3 (NOT to new^4 - hat^3). Carrying the same lines on (40-digit arithmetic)
+    # gives iteration 5 and the residual / decision sequence below; the momentum streak
+    # 2..7 ends in a restart at iteration 8 (c^8 = 0.0189793 > 0.999 c^7 = 0.0132236).
+    r5 = oracle.solve(inst, eps=-1.0, max_iters=5, accel=1)
+    _check_iterates(r5, [(1.3042030488894554, 0.1), (0.10518100701190204, 0.12807948256717436),
+                         (-0.30926275538916858, 0.89494029350028678),
+                         (0.30926275538916858, -0.44055765323350115),
+                         (-0.30926275538916858, 0.44055765323350115)], 2e-15)
+    r10 = oracle.solve(inst, eps=-1.0, max_iters=10, accel=1, history=True)
+    np.testing.assert_array_equal(r10["mask"], [0, 1, 1, 1, 1, 1, 1, 0, 1, 1])
+    np.testing.assert_allclose(
+        r10["c_hist"],
+        [1.9925, 0.255, 0.070138888888888889, 0.034698242066906957, 0.024775047451832719,
+         0.01650067174732074, 0.013236803707351405, 0.018979293279754719,
+         0.0089498935296779736, 0.0031235443201129231], rtol=1e-13, atol=0)
+    # After the restart at 8, alpha_8 = 1: iteration 9 takes momentum with factor 0 again and
+    # iteration 10 with (phi - 1)/alpha_3 (the alpha sequence starts over).
+    _check_iterates(r10, [(1.3415668319288078, 0.1), (0.0722366306786494, 0.076453214714245497),
+                          (-0.34058150835395322, 0.90098532357485459),
+                          (0.34058150835395322, -0.3469652210416442),
+                          (-0.34058150835395322, 0.3469652210416442)], 1e-14)
+
+
+def test_accelerated_restart_after_a_momentum_streak_by_hand():
+    # Same scalar case with eta = 0.4. Iterations 1-4 are those above (c^4 = 0.0346982);
+    # iteration 3 took momentum (c^3/c^2 = 0.275 <= 0.4), iteration 4 restarts
+    # (c^4/c^3 = 0.4947 > 0.4): alpha := 1, hats := new^4. Iteration 5 is then a plain step from
+    # the iteration-4 iterates; c^5 = 0.0217754 is compared with c^4 (the value computed in the
+    # restarting iteration), 0.0217754 > 0.4 * 0.0346982, so iteration 5 restarts as well (with a
+    # comparison value reset to c^0 = 1 it would wrongly take momentum). Ratios then run
+    # 0.551 (restart), 0.427 (restart), 0.332 (momentum, factor 0 since alpha = 1),
+    # 0.340 (momentum, factor (phi - 1)/alpha_3: alpha restarted from 1), 0.561 (restart).
+    inst = _scalar_inst()
+    r = oracle.solve(inst, eps=-1.0, max_iters=10, accel=1, eta=0.4, history=True)
+    np.testing.assert_array_equal(r["mask"], [0, 1, 1, 0, 0, 0, 0, 1, 1, 0])
+    np.testing.assert_allclose(
+        r["c_hist"],
+        [1.9925, 0.255, 0.070138888888888889, 0.034698242066906957, 0.021775415634775444,
+         0.011991158748049989, 0.0051179576332096188, 0.0017007691688496881,
+         0.00057744099740557136, 0.00032384853594166815], rtol=1e-13, atol=0)
+    r5 = oracle.solve(inst, eps=-1.0, max_iters=5, accel=1, eta=0.4)
+    _check_iterates(r5, [(1.2698613287114396, 0.1), (0.057231380213347481, 0.097300715857627703),
+                         (-0.29230653105127328, 0.87755479766016628),
+                         (0.29230653105127328, -0.43038391863076397),
+                         (-0.29230653105127328, 0.43038391863076397)], 2e-15)
+    r9 = oracle.solve(inst, eps=-1.0, max_iters=9, accel=1, eta=0.4)
+    _check_iterates(r9, [(1.3679444603362244, 0.1), (0.11875474239762131, 0.10978251222950911),
+                         (-0.36934728548246401, 0.89859717485376039),
+                         (0.36934728548246401, -0.35109508004423997),
+                         (-0.36934728548246401, 0.35109508004423997)], 1e-14)
