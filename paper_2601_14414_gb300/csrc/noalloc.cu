@@ -1,8 +1,9 @@
 // noalloc.cu -- pimpc_solve_static: one MPC instance solved without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA-graph capture region that
-// must not allocate, real-time control loops that forbid allocation after start-up, and hosts
-// whose allocator is owned by another framework. For them this entry point takes every input
+// Some callers cannot call cudaMalloc: real-time control loops that forbid allocation after
+// start-up (an allocation can synchronise the device and has no latency bound), controllers
+// certified without dynamic memory, and plug-ins inside a host whose device memory belongs to
+// another framework's allocator. For them this entry point takes every input
 // and output as device memory owned by the caller and keeps all of its own working memory
 // (stage blocks, iterates, per-instance state, work list, control block) in one file-scope
 // device array of fixed size, kStaticBytes. Every GPU that loads the library holds that array
@@ -16,6 +17,7 @@
 // The arithmetic is that of pimpc_solve: the same factorisation, solve and output kernels run
 // on the same memory layout, with their buffers carved out of the static array.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -124,8 +126,15 @@ extern "C" int pimpc_solve_static(int nx, int nu, int N, int precision, const do
     return fail_static(PIMPC_EINVAL, "pimpc_solve_static: bad precision");
   if (!A || !B || !q || !r || !xmin || !xmax || !umin || !umax || !x0)
     return fail_static(PIMPC_EINVAL, "pimpc_solve_static: missing input");
-  if (!(rho > 0.0) || max_iters < 0 || (accel != 0 && accel != 1))
-    return fail_static(PIMPC_EINVAL, "pimpc_solve_static: bad options");
+  // The same option checks as pimpc_set_options.
+  if (!(rho > 0.0) || !std::isfinite(rho))
+    return fail_static(PIMPC_EINVAL, "pimpc_solve_static: rho must be finite and > 0");
+  if (std::isnan(eps)) return fail_static(PIMPC_EINVAL, "pimpc_solve_static: eps is NaN");
+  if (max_iters < 0) return fail_static(PIMPC_EINVAL, "pimpc_solve_static: max_iters < 0");
+  if (accel != 0 && accel != 1)
+    return fail_static(PIMPC_EINVAL, "pimpc_solve_static: accel must be 0 or 1");
+  if (!(eta >= 0.0) || !std::isfinite(eta))
+    return fail_static(PIMPC_EINVAL, "pimpc_solve_static: eta must be finite and >= 0");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t ts = precision == PIMPC_F32 ? 4 : 8;
   const int64_t ntiles = (N + 31) / 32;
@@ -214,6 +223,7 @@ extern "C" int pimpc_solve_static(int nx, int nu, int N, int precision, const do
   a.ndone = v.ndone; a.stop = v.stop;
   a.u_out = u_out; a.x_out = x_out;
   a.warm = 0;  // cold start: the iterate buffer is cleared by the launch sequence
+  a.ferr = v.ferr;
   a.threads = tps_threads();
   a.nv_max = n;
   const size_t smem = tps_smem_bytes(n, precision);

@@ -1,10 +1,11 @@
 """pimpc_solve_static (the entry point that allocates no device memory) against pimpc_solve.
 
-Callers that cannot call cudaMalloc (graph-captured or real-time code, hosts whose allocator
-belongs to another framework) use pimpc_solve_static, which keeps its working memory in a fixed
-device array inside the library. Its results must equal those of the allocating entry point
-within the FP64 parity tolerance of the other GPU tests (1e-10), on two calls in a row (the
-second call reuses the array the first one left behind). This file is collected last.
+Callers that cannot call cudaMalloc (real-time control loops that forbid allocation after
+start-up, controllers certified without dynamic memory, plug-ins whose host owns the device
+allocator) use pimpc_solve_static, which keeps its working memory in a fixed device array inside
+the library. Its results must equal those of the allocating entry point within the parity
+tolerances of the other GPU tests (1e-10 in FP64, 1e-4 on u and x in FP32), on two calls in a
+row (the second call reuses the array the first one left behind). This file is collected last.
 """
 import numpy as np
 import pytest
@@ -22,7 +23,11 @@ def relerr(a, b):
 def run_static(inst, precision, eps, max_iters, accel):
     import torch
     dev = torch.device("cuda")
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(dev)
+
+    def t(a):
+        if a is None:
+            return None
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(dev)
     nx, nu, N = inst["nx"], inst["nu"], inst["N"]
     u = torch.zeros(N * nu, dtype=torch.float64, device=dev)
     x = torch.zeros(N * nx, dtype=torch.float64, device=dev)
@@ -63,3 +68,24 @@ def test_static_entry_point_rejects_instances_larger_than_its_array():
         run_static(inst, pimpc.F64, 1e-6, 10, 1)
     assert e.value.code == pimpc.EINVAL
     assert "static array" in str(e.value)
+
+
+def test_static_entry_point_fp32_matches_allocating_one_twice_in_a_row():
+    # FP32 iterations (one thread per stage on the tiled layout) at a fixed iteration count of
+    # the plain iteration, so that no discrete restart decision can differ: a nonzero constant
+    # reference, and one call without the affine term e (NULL = 0).
+    first = W.random_ltv(511, 8, 3, 100)
+    first["ref"] = np.linspace(-0.8, 0.9, first["nx"] + first["nu"])
+    second = W.random_ltv(512, 12, 4, 45)
+    second["ref"] = np.full(second["nx"] + second["nu"], 0.3)
+    second["e"] = None
+    for inst in (first, second):
+        us, xs, its, _, _ = run_static(inst, pimpc.F32, -1.0, 150, 0)
+        alloc = dict(inst)
+        if alloc["e"] is None:
+            alloc["e"] = np.zeros((inst["N"], inst["nx"]))
+        ua, xa, ita, _, _ = run_allocating(alloc, pimpc.F32, -1.0, 150, 0)
+        assert its == ita == 150
+        assert relerr(us, ua) <= 1e-4
+        assert relerr(xs, xa) <= 1e-4
+        assert np.max(np.abs(xs)) > 1e-3  # the reference moved the solution away from zero
