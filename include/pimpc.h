@@ -40,7 +40,14 @@ extern "C" {
 /* Return codes. */
 enum { PIMPC_OK = 0, PIMPC_EINVAL = 1, PIMPC_ENOMEM = 2, PIMPC_ECUDA = 3, PIMPC_ESTATE = 4 };
 /* Per-instance solve status. */
-enum { PIMPC_CONVERGED = 0, PIMPC_MAXITER = 1, PIMPC_NONFINITE = 2, PIMPC_TIMEOUT = 3 };
+enum {
+  PIMPC_CONVERGED = 0,      /* c^{i+1} <= eps (Algorithm 1 step 5)                          */
+  PIMPC_MAXITER = 1,        /* max_iters reached                                            */
+  PIMPC_NONFINITE = 2,      /* c^{i+1} is not finite                                        */
+  PIMPC_TIMEOUT = 3,        /* a bounded wait of the launch gave up before the instance ended */
+  PIMPC_FACTOR_FAILED = 4   /* the stage cache met a non-positive (or NaN) pivot: non-finite  */
+                            /* or overflowing dynamics; the instance's outputs are not valid  */
+};
 /* Arithmetic of the ADMM iterations (the factorisation is always FP64). */
 enum { PIMPC_F32 = 0, PIMPC_F64 = 1 };
 /* Memory space of caller buffers. */
@@ -141,7 +148,10 @@ int pimpc_get_dynamics(pimpc_solver *s, double *A, double *B, double *e, int mem
  *   H_k = (Qbar + rho I + rho Abar_{k+1}^T Abar_{k+1})^{-1} (k < N-1), H_{N-1} = (Qbar + rho I)^{-1}
  *   (definition after the velocity-form iteration) and M_k = (B_k^T B_k + I + Wdu / rho)^{-1},
  *   so that J_k v = M_k Bbar_k^T v, by Cholesky factorisation. Results are stored in the
- *   iteration precision. pimpc_solve calls it implicitly when the cache is stale.
+ *   iteration precision. pimpc_solve calls it implicitly when the cache is stale. With valid
+ *   weights and rho both matrices are >= I (symmetric positive definite), so a non-positive
+ *   pivot means non-finite or overflowing dynamics: the call stays asynchronous and the next
+ *   solve reports such instances with status PIMPC_FACTOR_FAILED.
  * Errors: PIMPC_ECUDA.
  */
 int pimpc_factorise(pimpc_solver *s, void *stream);
@@ -158,7 +168,7 @@ int pimpc_factorise(pimpc_solver *s, void *stream);
  *   u_out [sum N nu], x_out [sum N nx]   u_k and x_{k+1} read from z_{k+1} (inside the box);
  *                        either may be NULL.
  *   iters[batch], c[batch], status[batch]  iterations run, last c^{i+1}, PIMPC_CONVERGED /
- *                        MAXITER / NONFINITE; any may be NULL.
+ *                        MAXITER / NONFINITE / TIMEOUT / FACTOR_FAILED; any may be NULL.
  * Errors: PIMPC_EINVAL, PIMPC_ECUDA.
  */
 int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const double *ref,
@@ -224,6 +234,16 @@ int pimpc_get_stats(pimpc_solver *s, int *iters, double *c, int *status, int *mo
  */
 int pimpc_set_restart_mask(pimpc_solver *s, const unsigned char *mask, int len, int mem,
                            void *stream);
+
+/*
+ * pimpc_set_wait_limit -- bound of the grid-wide barrier of the persistent launch (testing aid,
+ * no counterpart in the paper): a CTA polls the barrier at most `polls` times (about 0.1 us
+ * each) before the launch gives up, stops every CTA at its next barrier and reports the
+ * instances it did not finish as PIMPC_TIMEOUT. 0 (the default) restores the built-in limit
+ * (about half a second). Affects the schedule families with a grid barrier (0, 2, 4, 5).
+ * Errors: PIMPC_EINVAL (polls < 0).
+ */
+int pimpc_set_wait_limit(pimpc_solver *s, int polls);
 
 /*
  * pimpc_plant_step -- one explicit-Euler step x_next = x + dt f(x, u) of a built-in model per
@@ -311,8 +331,9 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
  * pimpc_solve_static -- one instance, solved without allocating any device memory.
  *
  * No counterpart in the paper: this entry point exists for callers that cannot call cudaMalloc
- * (work recorded into a CUDA graph that must not allocate, real-time loops that forbid
- * allocation after start-up, hosts whose device allocator belongs to another framework). It
+ * (real-time control loops that forbid allocation after start-up, because an allocation can
+ * synchronise the device and has no latency bound; controllers certified without dynamic
+ * memory; plug-ins inside a host whose device memory belongs to another framework). It
  * computes what pimpc_create + set_* + pimpc_solve (cold start) compute for a single
  * stage-varying instance, with the same kernels, but its working memory is one file-scope
  * device array of PIMPC_STATIC_BYTES that every GPU loading the library holds until exit.
@@ -321,15 +342,19 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
  *   A [N nx nx], B [N nx nu], e [N nx] (NULL = 0), q [nx], r [nu], xmin, xmax [nx],
  *   umin, umax [nu], x0 [nx], ref [n] (constant reference, NULL = 0): DEVICE memory, FP64,
  *   owned by the caller, read during the call's kernels only.
- *   rho, eps, max_iters, accel, eta  as in pimpc_set_options.
+ *   rho, eps, max_iters, accel, eta  as in pimpc_set_options, with the same checks.
  *   u_out [N nu], x_out [N nx], iters[1], c[1], status[1]: DEVICE memory (any may be NULL).
  *   stream        cudaStream_t; the call only enqueues work on it.
  * The call allocates nothing (no cudaMalloc, no cudaFree, no allocating library call). Its
  * first call on a device looks up the array's address with cudaGetSymbolAddress; make that
  * first call before any stream capture. Every call shares the array and rewrites or clears what
  * it reads, so consecutive calls are independent, but calls that overlap on the GPU race.
- * Errors: PIMPC_EINVAL (sizes, or an instance whose working memory exceeds PIMPC_STATIC_BYTES;
- * the message is in pimpc_last_error(NULL)), PIMPC_ECUDA.
+ * Capacity: the working memory is about N * (W + 15 n) * ts bytes (ts = 4 in FP32, 8 in FP64;
+ * W = nx n + nx + n(n+1)/2 + nu(nu+1)/2 words of stage data, N rounded up to a multiple of 32),
+ * so at n = 32 the worst split (nx = 31, nu = 1, W = 1552) fits about 2000 stages in FP32 and
+ * 1000 in FP64.
+ * Errors: PIMPC_EINVAL (sizes, options, or an instance whose working memory exceeds
+ * PIMPC_STATIC_BYTES; the message is in pimpc_last_error(NULL)), PIMPC_ECUDA.
  */
 #define PIMPC_STATIC_BYTES (16u << 20)
 int pimpc_solve_static(int nx, int nu, int N, int precision, const double *A, const double *B,

@@ -45,7 +45,8 @@
 
 namespace pimpc {
 
-__global__ void set_control_kernel(Ctl *c, int nitems, int batch) {
+__global__ void set_control_kernel(Ctl *c, int nitems, int batch, int bar_limit) {
+  c->bar_limit = bar_limit;
   c->nlist[0] = nitems;
   c->nlist[1] = 0;
   c->active = batch;

@@ -560,6 +560,8 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.alpha = s->alpha; a.cprev = s->cprev; a.coef = s->coef; a.cacc = s->cacc;
   a.ndone = s->ndone; a.stop = s->stop;
   a.warm = warm_start;
+  a.ferr = s->ferr;
+  a.bar_limit = s->bar_limit;
   a.u_out = u_dev;
   a.x_out = x_dev;
   a.coef_tab = s->coef_tab;
@@ -830,7 +832,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(dalloc(s, &s->nitems_inst, sizeof(int) * 2 * batch));
   chk(dalloc(s, &s->ctl, sizeof(Ctl)));
   chk(dalloc(s, &s->binst, sizeof(int) * s->nblocks));
-  chk(dalloc(s, &s->ferr, sizeof(int) * 4));
+  chk(dalloc(s, &s->ferr, sizeof(int) * (size_t)batch));
   chk(dalloc(s, &s->st, sizeof(InstState) * batch));
   if (e != cudaSuccess) {
     g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
@@ -845,7 +847,7 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(cudaMemset(s->qd64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->rdu64, 0, sizeof(double) * s->tot_n));
   chk(cudaMemset(s->qd_T, 0, ts * s->tot_n));
-  chk(cudaMemset(s->ferr, 0, sizeof(int) * 4));
+  chk(cudaMemset(s->ferr, 0, sizeof(int) * (size_t)batch));
   chk(cudaMemset(s->st, 0, sizeof(InstState) * batch));
   {
     std::vector<double> inf(s->tot_n, INFINITY);
@@ -1168,6 +1170,14 @@ int pimpc_set_restart_mask(pimpc_solver *s, const unsigned char *mask, int len, 
   if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "mask");
   s->mask = buf;
   s->mask_len = len;
+  return PIMPC_OK;
+}
+
+int pimpc_set_wait_limit(pimpc_solver *s, int polls) {
+  if (!s) return PIMPC_EINVAL;
+  if (polls < 0) return fail(s, PIMPC_EINVAL, "polls must be >= 0");
+  graph_invalidate(s);
+  s->bar_limit = polls;
   return PIMPC_OK;
 }
 

@@ -25,7 +25,7 @@ struct FactArgs {
   const int64_t *bbase;      // first global block of each instance
   int64_t nblocks;
   int words_per_warp;        // shared-memory doubles per warp
-  int *err;                  // set to 1 on a non-positive pivot
+  int *err;                  // [batch]: set to 1 for an instance with a non-positive pivot
 };
 
 // Cholesky of the m x m matrix in S (lower triangle used, leading dimension ld) in place;
@@ -128,7 +128,7 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     if (i == c) s += qd[i] + rho;
     S[i * ld + c] = s;
   }
-  chol_inverse(S, X, G, n, ld, lane, a.err);  // G is rebuilt below: scratch for 1/L_ii
+  chol_inverse(S, X, G, n, ld, lane, a.err + j);  // G is rebuilt below: scratch for 1/L_ii
 
   const int W = a.L.W[j];
   const int lay = a.L.tiled;
@@ -216,7 +216,7 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     S[i * nu + c] = s;
   }
   __syncwarp();
-  chol_inverse(S, X, G, nu, nu, lane, a.err);  // G is not read again: scratch for 1/L_ii
+  chol_inverse(S, X, G, nu, nu, lane, a.err + j);  // G is not read again: scratch for 1/L_ii
   put_sym(oM, nu, X, nu);
   if (!packed) {  // padding of a plain or blocked block
     const int end = oM + wrapped_size(nu);
@@ -242,8 +242,9 @@ cudaError_t launch_factorise(const Layout &L, const double *A, const double *B, 
   if (wpc > 8) wpc = 8;
   const size_t smem = per_warp * wpc;
   const int64_t grid = (nblocks + wpc - 1) / wpc;
+  cudaError_t rc = cudaMemsetAsync(err, 0, sizeof(int) * (size_t)L.batch, stream);
+  if (rc != cudaSuccess) return rc;
   if (grid == 0) return cudaSuccess;
-  cudaError_t rc;
   if (precision == 0) {
     rc = cudaFuncSetAttribute(factorise_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);

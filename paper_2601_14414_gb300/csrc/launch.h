@@ -38,12 +38,14 @@ struct AdmmLaunch {
   const double *coef_tab;
   const int *grp;   // blocked kernel: lane groups per sub-chunk of each instance
   int warm;
+  const int *ferr;  // [batch] nonzero: the instance's factorisation met a non-positive pivot
+  int bar_limit;    // grid-barrier polls before giving up (0: the default limit)
   // launch shape and shared-memory plan (elements of the iteration type)
   int grid, threads;
   int capB, capI, haloB, haloI, S_max, nv_max, nbuf;
 };
 
-__global__ void set_control_kernel(Ctl *c, int nitems, int batch);
+__global__ void set_control_kernel(Ctl *c, int nitems, int batch, int bar_limit);
 int admm_threads(int precision);
 int admm_iter_stride(int n, int precision);
 int admm_group_size(int n);

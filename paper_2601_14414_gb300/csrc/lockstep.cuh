@@ -41,6 +41,7 @@ struct Args {
   int capI;
   const double *coef_tab;  // momentum factor of the m-th consecutive momentum step (resident)
   const int *grp;          // blocked kernel: lane groups per sub-chunk of each instance
+  const int *ferr;         // [batch] factorisation failure flags (may be null)
 };
 
 // Iterate element (vector b in {z, v, theta, beta, lambda}, component c) of stage k (its own
@@ -79,9 +80,11 @@ __device__ inline bool grid_sync(Ctl *c, unsigned nblocks, int *sOk) {
       __threadfence();
       atomicAdd(&c->bar_gen, 1u);
     } else {
+      const int lim = *(volatile int *)&c->bar_limit;
+      const long long limit = lim > 0 ? (long long)lim : kWaitLimit;
       long long k = 0;
       while (*gen == g) {
-        if (++k > kWaitLimit || *(volatile int *)&c->err) { ok = 0; break; }
+        if (++k > limit || *(volatile int *)&c->err) { ok = 0; break; }
         __nanosleep(100);
       }
     }
@@ -230,14 +233,18 @@ __global__ void prepare_kernel(Args<T> a, int warm, const int *old_base) {
   }
 }
 
-// u_k and x_{k+1} from z_{k+1} of the final iterate; instances the launch did not finish (a
-// timed-out wait) are reported as PIMPC_TIMEOUT.
+// u_k and x_{k+1} from z_{k+1} of the final iterate; instances whose stage cache met a
+// non-positive pivot are reported as PIMPC_FACTOR_FAILED, instances the launch did not finish
+// (a timed-out wait) as PIMPC_TIMEOUT.
 template <typename T>
 __global__ void output_kernel(Args<T> a, double *u_out, double *x_out) {
   const int j = blockIdx.y;
   const int nx = a.L.nx[j], nu = a.L.nu[j], n = nx + nu, N = a.L.N[j];
   const int n5p = iter_stride_plain(n, (int)sizeof(T));
-  if (blockIdx.x == 0 && threadIdx.x == 0 && !a.stop[j]) a.st[j].status = kTimeout;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (a.ferr && a.ferr[j]) a.st[j].status = kFactorFailed;
+    else if (!a.stop[j]) a.st[j].status = kTimeout;
+  }
   const T *z = a.it[a.base[j]] + a.L.Ni[j];
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -278,6 +285,7 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.capI = 0;
   a.coef_tab = s.coef_tab;
   a.grp = s.grp;
+  a.ferr = s.ferr;
   return a;
 }
 
@@ -297,7 +305,7 @@ cudaError_t launch_sequence(const AdmmLaunch &s, Args<T> &a, const void *kernel,
     prepare_kernel<T><<<dim3(8, s.L.batch), 256, 0, stream>>>(a, s.warm, s.old_base);
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
   }
-  set_control_kernel<<<1, 1, 0, stream>>>(s.ctl, s.nitems, s.L.batch);
+  set_control_kernel<<<1, 1, 0, stream>>>(s.ctl, s.nitems, s.L.batch, s.bar_limit);
   if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
   if (s.max_iters > 0) {
     rc = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -26,6 +26,7 @@ constexpr int kConverged = 0;   // per-instance status codes (same values as the
 constexpr int kMaxIter = 1;
 constexpr int kNonFinite = 2;
 constexpr int kTimeout = 3;
+constexpr int kFactorFailed = 4;
 constexpr int kMaxNLtv = 32;
 constexpr int kMaxNLti = 64;
 
@@ -55,7 +56,8 @@ struct Ctl {
   int err;               // nonzero: a bounded wait timed out
   int nlist[2];          // lengths of the two active-item lists
   int fine;              // the active list holds the fine items (one sub-chunk each)
-  int pad[6];
+  int bar_limit;         // polls of the grid barrier before it gives up (0: the default)
+  int pad[5];
 };
 
 __host__ __device__ inline int packed_size(int n) { return n * (n + 1) / 2; }

@@ -28,7 +28,7 @@ struct pimpc_solver {
   void *blk_T = nullptr, *qd_T = nullptr, *ref_T = nullptr;
   void *it[3] = {nullptr, nullptr, nullptr};
   void *lo_T = nullptr, *hi_T = nullptr, *xb0_T = nullptr;
-  int *base = nullptr, *old_base = nullptr, *binst = nullptr, *ferr = nullptr;
+  int *base = nullptr, *old_base = nullptr, *binst = nullptr, *ferr = nullptr;  // ferr: [batch]
   double *alpha = nullptr, *cprev = nullptr, *coef = nullptr, *cacc = nullptr;
   int *ndone = nullptr, *stop = nullptr;
   int *item_inst = nullptr, *item_a = nullptr, *item_b = nullptr, *nitems_inst = nullptr;
@@ -38,6 +38,7 @@ struct pimpc_solver {
   pimpc::InstState *st = nullptr;
   unsigned char *mask = nullptr, *mask_alloc = nullptr;
   int mask_len = 0;
+  int bar_limit = 0;  // grid-barrier polls before a launch gives up (0: the built-in limit)
   int nitems = 0;
   // options and state
   double rho = 1.0, eps = 1e-6, eta = 0.999;

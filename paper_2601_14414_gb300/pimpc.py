@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, 1, 2, 3, 4
-CONVERGED, MAXITER, NONFINITE, TIMEOUT = 0, 1, 2, 3
+CONVERGED, MAXITER, NONFINITE, TIMEOUT, FACTOR_FAILED = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 HOST, DEVICE = 0, 1
 MODEL_QUADROTOR, MODEL_CARTPOLE, MODEL_CSTR = 0, 1, 2
@@ -45,6 +45,7 @@ _SIGS = {
     "pimpc_get_iterates": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _VP]),
     "pimpc_get_stats": (_I, [_VP, _VP, _VP, _VP, _VP, _I, _VP]),
     "pimpc_set_restart_mask": (_I, [_VP, _VP, _I, _I, _VP]),
+    "pimpc_set_wait_limit": (_I, [_VP, _I]),
     "pimpc_plant_step": (_I, [_VP, _I, _VP, _D, _VP, _VP, _VP, _I, _VP]),
     "pimpc_backward": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP]),
     "pimpc_solve_static": (_I, [_I, _I, _I, _I] + [_VP] * 11 + [_D, _D, _I, _I, _D] + [_VP] * 6),
@@ -200,6 +201,10 @@ def pimpc_get_iterates(h, z=None, v=None, theta=None, beta=None, lam=None):
 def pimpc_get_stats(h, iters=None, c=None, status=None, momentum_iters=None):
     p, mem, st = _marshal(iters, c, status, momentum_iters)
     _check(h, load().pimpc_get_stats(h, *p, mem, st))
+
+
+def pimpc_set_wait_limit(h, polls):
+    _check(h, load().pimpc_set_wait_limit(h, int(polls)))
 
 
 def pimpc_set_restart_mask(h, mask, length):

@@ -63,3 +63,17 @@ def test_pack_layout_is_batch_then_stage_major():
     np.testing.assert_array_equal(p["A"][:36], insts[0]["A"].ravel())
     np.testing.assert_array_equal(p["A"][36:], insts[1]["A"].ravel())
     assert p["x0"].size == 3 + 5 and p["umax"].size == 1 + 2
+
+
+def test_static_entry_point_checks_options_like_set_options():
+    # Rejected before any device is touched (no GPU needed): the pointers are never read.
+    lib = pimpc.load()
+    buf = np.zeros(64)
+    ptr = ctypes.c_void_p(buf.ctypes.data)
+    inf, nan = float("inf"), float("nan")
+    for rho, eps, eta in ((inf, 1e-6, 0.999), (0.0, 1e-6, 0.999), (1.0, nan, 0.999),
+                          (1.0, 1e-6, -0.5), (1.0, 1e-6, nan), (1.0, 1e-6, inf)):
+        rc = lib.pimpc_solve_static(2, 1, 4, 0, *([ptr] * 11), ctypes.c_double(rho),
+                                    ctypes.c_double(eps), 10, 1, ctypes.c_double(eta),
+                                    *([None] * 5), None)
+        assert rc == pimpc.EINVAL, (rho, eps, eta)
