@@ -199,3 +199,58 @@ def cstr_nmpc(N=5000, dt=0.5, rho=1.0, tc_bounds=(250.0, 350.0)):
 def cstr_inlet_temperature(t_min):
     """T_i(t) = 298.15 + 5 sin(0.05 t) K (t in minutes)."""
     return 298.15 + 5.0 * np.sin(0.05 * t_min)
+
+
+# AFTI-16 aircraft, continuous-time linearised model printed in the paper's first example
+# (Sec. V-A): four states, two control surfaces, outputs y = (x_2, x_4) (attack and pitch angle).
+AFTI16_AC = np.array([[-0.0151, -60.5651, 0.0, -32.174],
+                      [-0.0001, -1.3411, 0.9929, 0.0],
+                      [0.00018, 43.2541, -0.86939, 0.0],
+                      [0.0, 0.0, 1.0, 0.0]])
+AFTI16_BC = np.array([[-2.516, -13.136],
+                      [-0.1689, -0.2514],
+                      [-17.251, -1.5766],
+                      [0.0, 0.0]])
+
+
+def zoh(Ac, Bc, dt, terms=40, squarings=8):
+    """Zero-order-hold discretisation: [[A, B], [0, I]] = exp([[Ac, Bc], [0, 0]] dt), the
+    exponential by scaling and squaring of a truncated Taylor series (input generation only)."""
+    nx, nu = Bc.shape
+    M = np.zeros((nx + nu, nx + nu))
+    M[:nx, :nx] = Ac
+    M[:nx, nx:] = Bc
+    M *= dt / 2.0 ** squarings
+    E = np.eye(nx + nu)
+    term = np.eye(nx + nu)
+    for k in range(1, terms):
+        term = term @ M / k
+        E = E + term
+    for _ in range(squarings):
+        E = E @ E
+    return E[:nx, :nx], E[:nx, nx:]
+
+
+def afti16(N=5, dt=0.05, rho=10.0, steps=200, amplitude=10.0, period=100):
+    """AFTI-16 tracking MPC of the paper's first example: ZOH at 0.05 s, |u_i| <= 25 (degrees),
+    |y_1| <= 0.5, |y_2| <= 100 (state bounds on x_2 and x_4, C selects them), W_y = diag(100, 100)
+    (so Q = C^T W_y C = diag(0, 100, 0, 100)), W_u = 0, W_du = diag(0.1, 0.1), N = 5, 200 MPC steps
+    from rest. The paper does not print the pitch reference r_2 or rho: here r_2 is a square wave
+    of +-amplitude degrees with the given period in steps (y_1 is regulated to 0), and rho = 10,
+    the value of {0.1, 1, 3, 5, 10, 20, 30, 100} with the fewest iterations on this reference."""
+    A, B = zoh(AFTI16_AC, AFTI16_BC, dt)
+    nx, nu = 4, 2
+    inf = np.inf
+    return dict(nx=nx, nu=nu, N=N, lti=True, A=A, B=B, e=np.zeros(nx),
+                q=np.array([0.0, 100.0, 0.0, 100.0]), r=np.zeros(nu), rdu=np.array([0.1, 0.1]),
+                xmin=np.array([-inf, -0.5, -inf, -100.0]), xmax=np.array([inf, 0.5, inf, 100.0]),
+                umin=-25.0 * np.ones(nu), umax=25.0 * np.ones(nu),
+                x0=np.zeros(nx), u_prev=np.zeros(nu), ref=np.zeros(nx + nu), rho=rho, dt=dt,
+                steps=steps, amplitude=amplitude, period=period)
+
+
+def afti16_reference(wl, step):
+    """Reference of xbar_{k+1} = (x, u) at MPC step `step`: pitch x_4 -> r_2(step), the rest 0."""
+    ref = np.zeros(wl["nx"] + wl["nu"])
+    ref[3] = wl["amplitude"] if (step // (wl["period"] // 2)) % 2 == 0 else -wl["amplitude"]
+    return ref
