@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 CONVERGED, MAXITER, NONFINITE = 0, 1, 2
+USET_BOX, USET_BALL2, USET_BALL1, USET_HALFSPACE, USET_SOC = 0, 1, 2, 3, 4
 MODEL_QUADROTOR, MODEL_CARTPOLE, MODEL_CSTR = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -40,7 +41,8 @@ class _Problem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nu", ctypes.c_int), ("N", ctypes.c_int),
                 ("A", _dp), ("B", _dp), ("e", _dp), ("q", _dp), ("r", _dp), ("rdu", _dp),
                 ("xmin", _dp), ("xmax", _dp), ("umin", _dp), ("umax", _dp),
-                ("x0", _dp), ("u_prev", _dp), ("ref", _dp), ("rho", ctypes.c_double)]
+                ("x0", _dp), ("u_prev", _dp), ("ref", _dp), ("rho", ctypes.c_double),
+                ("uset", ctypes.c_int), ("uset_r", ctypes.c_double), ("uset_a", _dp)]
 
 
 class _Options(ctypes.Structure):
@@ -71,6 +73,7 @@ def _load():
         lib.orc_cache.argtypes = [P, _dp, _dp]
         lib.orc_iteration.argtypes = [P, _dp, _dp] + [_dp] * 5 + [_dp] * 7 + [_dp]
         lib.orc_solve.argtypes = [P, ctypes.POINTER(_Options)] + [_dp] * 7 + [_ip, _dp, _ip, _dp, _up]
+        lib.orc_project_u.argtypes = [P, _dp, _dp]
         lib.orc_model_dims.argtypes = [ctypes.c_int, _ip, _ip]
         lib.orc_model_f.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp]
         lib.orc_linearise.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp,
@@ -117,11 +120,25 @@ class _Bound:
                          x0=_f64(inst["x0"]),
                          u_prev=None if inst.get("u_prev") is None else _f64(inst["u_prev"]),
                          ref=reference(inst))
+        us = inst.get("uset") or dict(kind=USET_BOX, r=0.0, a=None)
+        self.keep["uset_a"] = None if us.get("a") is None else _f64(us["a"])
         k = self.keep
         self.s = _Problem(inst["nx"], inst["nu"], inst["N"], _ptr(k["A"]), _ptr(k["B"]),
                           _ptr(k["e"]), _ptr(k["q"]), _ptr(k["r"]), _ptr(k["rdu"]),
                           _ptr(k["xmin"]), _ptr(k["xmax"]), _ptr(k["umin"]), _ptr(k["umax"]),
-                          _ptr(k["x0"]), _ptr(k["u_prev"]), _ptr(k["ref"]), float(inst["rho"]))
+                          _ptr(k["x0"]), _ptr(k["u_prev"]), _ptr(k["ref"]), float(inst["rho"]),
+                          int(us["kind"]), float(us.get("r", 0.0)), _ptr(k["uset_a"]))
+
+
+def project_u(inst, y):
+    """Euclidean projection of y [nu] onto the instance's input set."""
+    lib = _load()
+    pb = _Bound(inst)
+    y = _f64(y)
+    out = np.zeros(inst["nu"])
+    if lib.orc_project_u(ctypes.byref(pb.s), _ptr(y), _ptr(out)):
+        raise RuntimeError("oracle: unknown input set")
+    return out
 
 
 def cache(inst):

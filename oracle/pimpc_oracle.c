@@ -34,6 +34,9 @@
  *       Algorithm 1 exactly.
  *   R9  projection onto the box is min(max(y, lo), hi).
  *   R10 no separate terminal weight: stage N-1 uses the same Qbar.
+ *   R11 non-box input sets (the remark after Theorem 1): the reduced (v, z) problem has the
+ *       Hessian (3/2) I whatever the set, so z_{k+1} is the Euclidean projection of the same
+ *       point; the state part keeps its box, the input part is projected onto U as a vector.
  */
 #include "pimpc_oracle.h"
 
@@ -142,6 +145,85 @@ static void qbar_diag(const orc_problem *p, double *Qd) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Euclidean projections onto the input set U (textbook forms).                                */
+/* ------------------------------------------------------------------------------------------ */
+
+static int cmp_desc(const void *a, const void *b) {
+  const double x = *(const double *)a, y = *(const double *)b;
+  return (x < y) - (x > y);
+}
+
+int orc_project_u(const orc_problem *p, const double *y, double *out) {
+  const int m = p->nu;
+  const double r = p->uset_r;
+  switch (p->uset) {
+    case ORC_USET_BOX:
+      for (int i = 0; i < m; ++i) out[i] = fmin(fmax(y[i], p->umin[i]), p->umax[i]);
+      return 0;
+    case ORC_USET_BALL2: {          /* y min(1, r / ||y||) */
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += y[i] * y[i];
+      const double nrm = sqrt(s);
+      const double f = nrm <= r ? 1.0 : r / nrm;
+      for (int i = 0; i < m; ++i) out[i] = y[i] * f;
+      return 0;
+    }
+    case ORC_USET_BALL1: {          /* soft threshold at tau (Duchi et al. 2008, sorted form) */
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += fabs(y[i]);
+      if (s <= r) {
+        for (int i = 0; i < m; ++i) out[i] = y[i];
+        return 0;
+      }
+      double *a = (double *)malloc(sizeof(double) * (size_t)m);
+      if (!a) return -1;
+      for (int i = 0; i < m; ++i) a[i] = fabs(y[i]);
+      qsort(a, (size_t)m, sizeof(double), cmp_desc);
+      double run = 0.0, tau = 0.0;
+      for (int j = 0; j < m; ++j) {   /* largest j with a_j - (sum_{i<=j} a_i - r) / (j+1) > 0 */
+        run += a[j];
+        const double t = (run - r) / (double)(j + 1);
+        if (a[j] - t > 0.0) tau = t;
+      }
+      free(a);
+      for (int i = 0; i < m; ++i) {
+        const double mag = fabs(y[i]) - tau;
+        out[i] = mag > 0.0 ? copysign(mag, y[i]) : 0.0;
+      }
+      return 0;
+    }
+    case ORC_USET_HALFSPACE: {      /* y - max(0, a^T y - r) / ||a||^2 a */
+      double ay = 0.0, aa = 0.0;
+      for (int i = 0; i < m; ++i) {
+        ay += p->uset_a[i] * y[i];
+        aa += p->uset_a[i] * p->uset_a[i];
+      }
+      const double f = ay > r ? (ay - r) / aa : 0.0;
+      for (int i = 0; i < m; ++i) out[i] = y[i] - f * p->uset_a[i];
+      return 0;
+    }
+    case ORC_USET_SOC: {            /* cone {(t, s): ||s|| <= t}, t = y_0 */
+      const double t = y[0];
+      double s2 = 0.0;
+      for (int i = 1; i < m; ++i) s2 += y[i] * y[i];
+      const double ns = sqrt(s2);
+      if (ns <= t) {
+        for (int i = 0; i < m; ++i) out[i] = y[i];
+      } else if (ns <= -t) {
+        for (int i = 0; i < m; ++i) out[i] = 0.0;
+      } else {
+        const double al = 0.5 * (t + ns);
+        out[0] = al;
+        for (int i = 1; i < m; ++i) out[i] = al * y[i] / ns;
+      }
+      return 0;
+    }
+    default:
+      return -1;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Cache (Algorithm 1, "cache").                                                               */
 /* ------------------------------------------------------------------------------------------ */
 
@@ -212,9 +294,13 @@ int orc_iteration(const orc_problem *p, const double *H, const double *J, const 
   double *x0b = (double *)malloc(sizeof(double) * n);
   double *ax = (double *)malloc(sizeof(double) * n);
   double *bd = (double *)malloc(sizeof(double) * n);
-  if (!Abar || !Bbar || !ebar || !Qd || !t || !y || !Aty || !h || !x0b || !ax || !bd) {
+  double *gam = (double *)malloc(sizeof(double) * n);
+  double *wv = (double *)malloc(sizeof(double) * n);
+  double *zp = (double *)malloc(sizeof(double) * n);
+  if (!Abar || !Bbar || !ebar || !Qd || !t || !y || !Aty || !h || !x0b || !ax || !bd || !gam ||
+      !wv || !zp) {
     free(Abar); free(Bbar); free(ebar); free(Qd); free(t); free(y); free(Aty); free(h);
-    free(x0b); free(ax); free(bd);
+    free(x0b); free(ax); free(bd); free(gam); free(wv); free(zp);
     return -1;
   }
   qbar_diag(p, Qd);
@@ -252,11 +338,20 @@ int orc_iteration(const orc_problem *p, const double *H, const double *J, const 
     mat_vec(n, n, Abar, xprev, ax);                      /* Abar_k xbar_k   */
     mat_vec(n, nu, Bbar, du + (size_t)k * nu, bd);       /* Bbar_k du_k     */
     for (int i = 0; i < n; ++i) {
-      double lo = (i < nx) ? p->xmin[i] : p->umin[i - nx];
-      double hi = (i < nx) ? p->xmax[i] : p->umax[i - nx];
-      double gamma = bd[i] + beh[o + i] - ax[i] - ebar[i] + lah[o + i];
-      double w = (2.0 * (xb[o + i] + thh[o + i] + ax[i] + ebar[i] - lah[o + i]) + gamma) / 3.0;
-      double zi = fmin(fmax(w, lo), hi);                 /* [reading R9] */
+      gam[i] = bd[i] + beh[o + i] - ax[i] - ebar[i] + lah[o + i];
+      wv[i] = (2.0 * (xb[o + i] + thh[o + i] + ax[i] + ebar[i] - lah[o + i]) + gam[i]) / 3.0;
+    }
+    /* z_{k+1} = Proj_Xbar(w): the box on the state part [reading R9], U on the input part
+     * [reading R11]. */
+    for (int i = 0; i < nx; ++i) zp[i] = fmin(fmax(wv[i], p->xmin[i]), p->xmax[i]);
+    if (orc_project_u(p, wv + nx, zp + nx)) {
+      free(Abar); free(Bbar); free(ebar); free(Qd); free(t); free(y); free(Aty); free(h);
+      free(x0b); free(ax); free(bd); free(gam); free(wv); free(zp);
+      return -1;
+    }
+    for (int i = 0; i < n; ++i) {
+      double gamma = gam[i];
+      double zi = zp[i];
       double vi = 0.5 * (zi + gamma);
       z[o + i] = zi;
       v[o + i] = vi;
@@ -280,7 +375,7 @@ int orc_iteration(const orc_problem *p, const double *H, const double *J, const 
   }
   *c = rho * csum;
   free(Abar); free(Bbar); free(ebar); free(Qd); free(t); free(y); free(Aty); free(h);
-  free(x0b); free(ax); free(bd);
+  free(x0b); free(ax); free(bd); free(gam); free(wv); free(zp);
   return 0;
 }
 

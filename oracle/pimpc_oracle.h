@@ -15,6 +15,12 @@
  *   ref[N][n]       reference for xbar_{k+1} = (x_{k+1}, u_k); qbar_k = Qbar * ref[k].
  *   bounds          the box Xbar = X x U of Theorem 2: lo = (xmin, umin), hi = (xmax, umax);
  *                   +-INFINITY allowed.
+ *   uset            the input set U (the remark after Theorem 1: the (v, z) update stays a
+ *                   Euclidean projection for any closed convex set): ORC_USET_BOX (the box
+ *                   [umin, umax], the default), ORC_USET_BALL2 (||u||_2 <= uset_r),
+ *                   ORC_USET_BALL1 (||u||_1 <= uset_r), ORC_USET_HALFSPACE (uset_a^T u <=
+ *                   uset_r, uset_a[nu] nonzero), ORC_USET_SOC (||u_{1:nu-1}||_2 <= u_0, the
+ *                   second-order cone); umin and umax are ignored for the non-box sets.
  *   iterates        array index k holds: z[k] = z_{k+1}, v[k] = v_k, th[k] = theta_k,
  *                   be[k] = beta_k, la[k] = lambda_k (all [N][n]), du[k] = du_k ([N][nu]),
  *                   xb[k] = xbar_{k+1} ([N][n]).
@@ -34,7 +40,13 @@ typedef struct {
   const double *x0, *u_prev;
   const double *ref;
   double rho;
+  int uset;
+  double uset_r;
+  const double *uset_a;
 } orc_problem;
+
+enum { ORC_USET_BOX = 0, ORC_USET_BALL2 = 1, ORC_USET_BALL1 = 2, ORC_USET_HALFSPACE = 3,
+       ORC_USET_SOC = 4 };
 
 typedef struct {
   double eps;                      /* stop when c^{i+1} <= eps (Algorithm 1, step 5)       */
@@ -45,6 +57,9 @@ typedef struct {
 } orc_options;
 
 enum { ORC_CONVERGED = 0, ORC_MAXITER = 1, ORC_NONFINITE = 2 };
+
+/* Euclidean projection of y[nu] onto the input set of p (out[nu]). Returns 0 or -1. */
+int orc_project_u(const orc_problem *p, const double *y, double *out);
 
 /* Explicit per-stage cache of Algorithm 1: H[N][n][n] and J[N][nu][n]. Returns 0 or -1. */
 int orc_cache(const orc_problem *p, double *H, double *J);

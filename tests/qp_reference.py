@@ -12,6 +12,8 @@
                           least-squares solve for p, a bounded least-squares solve for q
                           (scipy lsq_linear, BVLS), the dual update and the residual
                           c = rho ||s+ - s||^2 + rho ||G (q+ - q)||^2.
+* ``generic_admm_step_set``, ``solve_set_qp`` -- the same with the inputs in a non-box convex set
+                          (l2 ball, l1 ball, halfspace, second-order cone), by SLSQP.
 """
 from __future__ import annotations
 
@@ -229,3 +231,107 @@ def generic_admm_step(sys_, rho, qhat, shat):
     s = shat + F @ p + G @ q - h
     c = rho * np.sum((s - shat) ** 2) + rho * np.sum((G @ (q - qhat)) ** 2)
     return p, q, s, c
+
+
+# ---------------------------------------------------------------------------------------------
+# Non-box input sets (the remark after Theorem 1): the same references with u_k in a convex set,
+# solved by a general nonlinear-programming routine (scipy SLSQP) instead of a closed form.
+# ---------------------------------------------------------------------------------------------
+
+def set_constraints(inst, u_slices):
+    """scipy constraint dicts keeping every u-slice of the variable vector in the instance's
+    input set. Smooth descriptions: ||u||^2 <= r^2; the l1 ball as the 2^nu inequalities
+    s'u <= r over sign vectors s; a'u <= r; t >= 0 and t^2 >= ||s||^2 for the cone."""
+    us = inst["uset"]
+    kind, r = us["kind"], float(us.get("r", 0.0))
+    nu = inst["nu"]
+    cons = []
+    for sl in u_slices:
+        if kind == 1:
+            cons.append(dict(type="ineq", fun=lambda y, sl=sl: r * r - np.sum(y[sl] ** 2),
+                             jac=lambda y, sl=sl: _grad_at(y, sl, -2.0 * y[sl])))
+        elif kind == 2:
+            for signs in itertools.product((-1.0, 1.0), repeat=nu):
+                sv = np.array(signs)
+                cons.append(dict(type="ineq", fun=lambda y, sl=sl, sv=sv: r - sv @ y[sl],
+                                 jac=lambda y, sl=sl, sv=sv: _grad_at(y, sl, -sv)))
+        elif kind == 3:
+            a = np.asarray(us["a"], float)
+            cons.append(dict(type="ineq", fun=lambda y, sl=sl: r - a @ y[sl],
+                             jac=lambda y, sl=sl: _grad_at(y, sl, -a)))
+        elif kind == 4:
+            def cone(y, sl=sl):
+                u = y[sl]
+                return u[0] * u[0] - np.sum(u[1:] ** 2)
+
+            def cone_jac(y, sl=sl):
+                u = y[sl]
+                return _grad_at(y, sl, np.concatenate([[2.0 * u[0]], -2.0 * u[1:]]))
+            cons.append(dict(type="ineq", fun=cone, jac=cone_jac))
+            cons.append(dict(type="ineq", fun=lambda y, sl=sl: y[sl][0],
+                             jac=lambda y, sl=sl: _grad_at(y, sl, np.eye(nu)[0])))
+        else:
+            raise ValueError("not a non-box set")
+    return cons
+
+
+def _grad_at(y, sl, g):
+    out = np.zeros_like(y)
+    out[sl] = g
+    return out
+
+
+def _slsqp(fun, jac, x0, bounds, cons):
+    from scipy.optimize import minimize
+    res = minimize(fun, x0, jac=jac, method="SLSQP", bounds=bounds, constraints=cons,
+                   options=dict(ftol=1e-16, maxiter=2000))
+    return res.x
+
+
+def generic_admm_step_set(sys_, rho, qhat, shat, inst):
+    """generic_admm_step with g = indicator of {z_{k+1} = (x, u): x in the box, u in U}: the
+    q-update is the same constrained least-squares problem, solved by SLSQP."""
+    F, G, h, Pf, cf = sys_["F"], sys_["G"], sys_["h"], sys_["Pf"], sys_["cf"]
+    lhs = Pf + rho * F.T @ F
+    rhs = -cf - rho * F.T @ (G @ qhat - h + shat)
+    p = np.linalg.solve(lhs, rhs)
+    b = h - F @ p - shat
+    nx, nu, N = inst["nx"], inst["nu"], inst["N"]
+    n = nx + nu
+    bounds = []
+    for i in range(2 * N * n):
+        lo, hi = sys_["lb"][i], sys_["ub"][i]
+        in_z_u = i >= N * n and (i - N * n) % n >= nx
+        bounds.append((None, None) if in_z_u else
+                      (None if not np.isfinite(lo) else lo, None if not np.isfinite(hi) else hi))
+    u_sl = [slice(N * n + k * n + nx, N * n + (k + 1) * n) for k in range(N)]
+    GtG, Gtb = G.T @ G, G.T @ b
+    q0 = np.linalg.lstsq(G, b, rcond=None)[0]
+    q = _slsqp(lambda y: 0.5 * y @ GtG @ y - Gtb @ y, lambda y: GtG @ y - Gtb, q0, bounds,
+               set_constraints(inst, u_sl))
+    s = shat + F @ p + G @ q - h
+    c = rho * np.sum((s - shat) ** 2) + rho * np.sum((G @ (q - qhat)) ** 2)
+    return p, q, s, c
+
+
+def solve_set_qp(inst):
+    """The MPC problem of Sec. II with u_k in the instance's input set (and the state box), in
+    y = (u_0, x_1, ..., u_{N-1}, x_N), solved by SLSQP."""
+    P, c, Aeq, beq, lb, ub, idx = original_qp(inst)
+    N = inst["N"]
+    bounds = []
+    dim = len(c)
+    u_idx = np.zeros(dim, bool)
+    for k in range(N):
+        u_idx[idx(k, "u")] = True
+    for i in range(dim):
+        if u_idx[i]:
+            bounds.append((None, None))
+        else:
+            bounds.append((None if not np.isfinite(lb[i]) else lb[i],
+                           None if not np.isfinite(ub[i]) else ub[i]))
+    cons = set_constraints(inst, [idx(k, "u") for k in range(N)])
+    cons.append(dict(type="eq", fun=lambda y: Aeq @ y - beq, jac=lambda y: Aeq))
+    y0 = equality_qp(P, c, Aeq, beq)[0]
+    y = _slsqp(lambda y: 0.5 * y @ P @ y + c @ y, lambda y: P @ y + c, y0, bounds, cons)
+    return y, idx
