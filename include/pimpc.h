@@ -23,8 +23,9 @@
  *   - Ownership: the caller owns every buffer it passes and may free or reuse it when the call
  *     returns (host memory) or when the stream has passed the call (device memory). The solver
  *     owns all device state (matrices, caches, iterates); pimpc_create allocates all of it
- *     except the adjoint's checkpoint store, which the first pimpc_backward call allocates, and
- *     the buffer of the testing aid pimpc_set_restart_mask; pimpc_destroy frees everything.
+ *     except the adjoint's checkpoint store, which the first pimpc_backward call allocates, the
+ *     input-set arrays (first pimpc_set_input_set call) and the buffer of the testing aid
+ *     pimpc_set_restart_mask; pimpc_destroy frees everything.
  *   - Errors: a nonzero return means the call did nothing (arguments are validated before any
  *     launch) except PIMPC_ECUDA, which reports a CUDA error; pimpc_last_error(s) then holds a
  *     message. Non-convergence is not an error: it is reported per instance in `status`.
@@ -45,8 +46,9 @@ enum {
   PIMPC_MAXITER = 1,        /* max_iters reached                                            */
   PIMPC_NONFINITE = 2,      /* c^{i+1} is not finite                                        */
   PIMPC_TIMEOUT = 3,        /* a bounded wait of the launch gave up before the instance ended */
-  PIMPC_FACTOR_FAILED = 4   /* the stage cache met a non-positive (or NaN) pivot: non-finite  */
+  PIMPC_FACTOR_FAILED = 4,  /* the stage cache met a non-positive (or NaN) pivot: non-finite  */
                             /* or overflowing dynamics; the instance's outputs are not valid  */
+  PIMPC_STALLED = 5         /* c stopped decreasing (pimpc_set_stall): the arithmetic's floor */
 };
 /* Arithmetic of the ADMM iterations (the factorisation is always FP64). */
 enum { PIMPC_F32 = 0, PIMPC_F64 = 1 };
@@ -168,7 +170,8 @@ int pimpc_factorise(pimpc_solver *s, void *stream);
  *   u_out [sum N nu], x_out [sum N nx]   u_k and x_{k+1} read from z_{k+1} (inside the box);
  *                        either may be NULL.
  *   iters[batch], c[batch], status[batch]  iterations run, last c^{i+1}, PIMPC_CONVERGED /
- *                        MAXITER / NONFINITE / TIMEOUT / FACTOR_FAILED; any may be NULL.
+ *                        MAXITER / NONFINITE / TIMEOUT / FACTOR_FAILED / STALLED; any may
+ *                        be NULL.
  * Errors: PIMPC_EINVAL, PIMPC_ECUDA.
  */
 int pimpc_solve(pimpc_solver *s, const double *x0, const double *u_prev, const double *ref,
@@ -234,6 +237,43 @@ int pimpc_get_stats(pimpc_solver *s, int *iters, double *c, int *status, int *mo
  */
 int pimpc_set_restart_mask(pimpc_solver *s, const unsigned char *mask, int len, int mem,
                            void *stream);
+
+/*
+ * pimpc_set_input_set -- the input part of Xbar = X x U as a non-box convex set (the remark after
+ * Theorem 1: the (v, z) update of the splitting stays a Euclidean projection for any closed
+ * convex set, so only the projection of z's input part changes). Per instance:
+ *   kind[batch]  0: the box [umin, umax] (pimpc_set_bounds; the default), 1: l2 ball
+ *                ||u||_2 <= r, 2: l1 ball ||u||_1 <= r, 3: halfspace a^T u <= r, 4: second-order
+ *                cone ||(u_1, .., u_{nu-1})||_2 <= u_0. For kinds 1-4 the input box is not used;
+ *                the state box always is.
+ *   r[batch]     radius (kinds 1, 2: finite, >= 0) or offset (kind 3: finite); unused otherwise.
+ *   a[sum nu]    halfspace normals (kind 3: finite, nonzero); may be NULL if no instance has
+ *                kind 3.
+ * Sets hold for every stage of the instance. Schedules: families 0 and 5 (the defaults) only;
+ * pimpc_set_schedule and pimpc_autotune keep to them while a non-box set is in force, and
+ * pimpc_backward (box only) returns PIMPC_ESTATE. The first call allocates the set arrays. The
+ * call synchronises `stream`.
+ * Errors: PIMPC_EINVAL (a bad kind or parameter, or a schedule family other than 0 or 5 in
+ * force), PIMPC_ENOMEM, PIMPC_ECUDA.
+ */
+int pimpc_set_input_set(pimpc_solver *s, const int *kind, const double *r, const double *a,
+                        int mem, void *stream);
+
+/*
+ * pimpc_set_stall -- a second stop test beside Algorithm 1's c <= eps (no counterpart in the
+ * paper; for FP32 iterations): once an instance's c^{i+1} has come below `below` (first at
+ * iteration i0), it also stops, with status PIMPC_STALLED, when c has not fallen below factor x
+ * the smallest c seen since for max(window, rel x i0) consecutive iterations (an instance that
+ * needed many iterations to get there converges slowly and keeps improving its iterates for
+ * longer after its c has levelled off). In FP32 the residual c of a slowly converging instance levels
+ * off where the rounding of the iterates outweighs their change (about 1e-11 to 1e-10 on the
+ * batched workloads) while its iterates are already as accurate as FP32 makes them; a tolerance
+ * eps set below that floor then ends such instances here instead of at max_iters. `below` keeps
+ * the plateaus of the accelerated iteration far above the floor from counting. window = 0 (the
+ * default) turns the test off. Errors: PIMPC_EINVAL (window < 0, factor outside (0, 1],
+ * below < 0 or NaN, rel < 0 or not finite).
+ */
+int pimpc_set_stall(pimpc_solver *s, int window, double factor, double below, double rel);
 
 /*
  * pimpc_set_wait_limit -- bound of the grid-wide barrier of the persistent launch (testing aid,

@@ -502,6 +502,7 @@ extern "C" int pimpc_backward(pimpc_solver *s, const double *dL_du, const double
     return fail(s, PIMPC_ESTATE,
                 "the last solve must use warm_start = 0, accel = 0 and eps < 0 (fixed iterations)");
   if (s->tiled == 1) return fail(s, PIMPC_ESTATE, "the adjoint does not read the 32-stage tiled layout");
+  if (s->any_uset) return fail(s, PIMPC_ESTATE, "the adjoint covers box input sets only");
   cudaStream_t st = (cudaStream_t)stream;
   cudaSetDevice(s->device);
   const int Tn = s->last_iters_fixed;

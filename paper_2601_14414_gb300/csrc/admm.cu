@@ -40,6 +40,7 @@
 #include <algorithm>
 
 #include "bulk.cuh"
+#include "usets.cuh"
 #include "lockstep.cuh"
 #include "products.cuh"
 
@@ -155,6 +156,9 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
       const T *ref = a.ref ? (a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j])) : nullptr;
       const int refstride = a.ref_per_stage ? n : 0;
       const T *lo = a.lo + a.L.off_n[j], *hi = a.hi + a.L.off_n[j];
+      const int ukind = a.uset_kind ? a.uset_kind[j] : uset::kUsetBox;  // input set U
+      const T ur = a.uset_kind ? a.uset_r[j] : (T)0;
+      const T *ua = a.uset_a ? a.uset_a + a.L.off_n[j] : nullptr;
       const int grp = tid / g, l = tid - grp * g;
       const unsigned gmask = g == 32 ? 0xffffffffu : (((1u << g) - 1u) << ((tid & 31) & ~(g - 1)));
       const int ncl = (g == 32 && n > 32) ? 2 : 1;
@@ -336,11 +340,13 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
         if (!__syncthreads_and(arrived)) { ok = false; break; }  // uniform across the CTA
 
         // ---- phase 2: steps 2-4 ----
-        if (active) {
+        {
           const T *xk = Xc + grp * nv;
           const T *xk1 = Xc + (grp + 1) * nv;
           T *o = In + (int64_t)k * n5p;
-          for (int qq = 0; qq < ncl; ++qq) {
+          T wv[2] = {(T)0, (T)0}, gv[2], axv[2], bdv[2], eev[2], xnv[2], av[2] = {(T)0, (T)0};
+          int cv[2] = {-1, -1};
+          for (int qq = 0; qq < ncl && active; ++qq) {
             const int c = l + 32 * qq;
             if (c < n) {
               T ax, bd, ee;
@@ -353,9 +359,22 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
                 ax = xk[c]; bd = sDU[c - nx]; ee = (T)0;
               }
               const T xn = xk1[c];
-              const T gam = bd + beh[qq] - ax - ee + lah[qq];
-              const T w = ((T)2 * (xn + thh[qq] + ax + ee - lah[qq]) + gam) / (T)3;
-              const T z = clampv(w, lo[c], hi[c]);
+              cv[qq] = c;
+              axv[qq] = ax; bdv[qq] = bd; eev[qq] = ee; xnv[qq] = xn;
+              gv[qq] = bd + beh[qq] - ax - ee + lah[qq];
+              wv[qq] = ((T)2 * (xn + thh[qq] + ax + ee - lah[qq]) + gv[qq]) / (T)3;
+              if (ukind == uset::kUsetHalfspace) av[qq] = ua[c];
+            }
+          }
+          // Input part onto a non-box set U (warp-wide; the kind is the same for the CTA's item).
+          if (ukind != uset::kUsetBox)
+            uset::project_inputs<T, 2>(ukind, ur, av, wv, cv, nx, n, g,
+                                       [](int jj) { return jj & 31; }, [](int jj) { return jj >> 5; });
+          for (int qq = 0; qq < ncl && active; ++qq) {
+            const int c = cv[qq];
+            if (c >= 0) {
+              const T ax = axv[qq], bd = bdv[qq], ee = eev[qq], xn = xnv[qq], gam = gv[qq];
+              const T z = (c < nx || ukind == uset::kUsetBox) ? clampv(wv[qq], lo[c], hi[c]) : wv[qq];
               const T v = (T)0.5 * (z + gam);
               const T th = thh[qq] + xn - z;
               const T be = beh[qq] + bd - v;

@@ -32,6 +32,7 @@
 #include <algorithm>
 
 #include "bulk.cuh"
+#include "usets.cuh"
 #include "lockstep.cuh"
 #include "products.cuh"
 
@@ -204,6 +205,9 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       const T *ref = a.ref ? (a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j])) : nullptr;
       const int refstride = a.ref_per_stage ? n : 0;
       const T *lo = a.lo + a.L.off_n[j], *hi = a.hi + a.L.off_n[j];
+      const int ukind = a.uset_kind ? a.uset_kind[j] : uset::kUsetBox;  // input set U
+      const T ur = a.uset_kind ? a.uset_r[j] : (T)0;
+      const T *ua = a.uset_a ? a.uset_a + a.L.off_n[j] : nullptr;
       const int grp = tid / g, l = tid - grp * g;
       const int c0 = 4 * l;
       const bool own = c0 < n;
@@ -432,24 +436,46 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           }
         }
         __syncwarp();
-        if (stage && own) {
-          const T *xk = Xc + grp * nP, *xk1 = Xc + (grp + 1) * nP;
-          const V4<T> x1 = ld4(xk1 + c0), x0 = ld4(xk + c0), du4 = ld4(sDU + c0);
-          const V4<T> ax4 = ld4(sY + c0), bd4 = ld4(sW + c0);
+        {
+          // w of the owned components (stage && own), the input part projected onto a non-box
+          // set U (warp-wide; the kind is the same for the CTA's item), then steps 2-4.
+          const bool mine = stage && own;
+          T wv[4] = {(T)0, (T)0, (T)0, (T)0}, gv[4], axv[4], bdv[4], eev[4], xnv[4];
+          T av[4] = {(T)0, (T)0, (T)0, (T)0};
+          int cv[4] = {-1, -1, -1, -1};
+          if (mine) {
+            const T *xk = Xc + grp * nP, *xk1 = Xc + (grp + 1) * nP;
+            const V4<T> x1 = ld4(xk1 + c0), x0 = ld4(xk + c0), du4 = ld4(sDU + c0);
+            const V4<T> ax4 = ld4(sY + c0), bd4 = ld4(sW + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int c = c0 + i;
+              if (c < n) {
+                const bool xs = c < nx;
+                axv[i] = xs ? ax4.v[i] : x0.v[i];
+                bdv[i] = xs ? bd4.v[i] : du4.v[i];
+                eev[i] = e4.v[i];
+                xnv[i] = x1.v[i];
+                gv[i] = bdv[i] + bh.v[i] - axv[i] - eev[i] + lh.v[i];
+                wv[i] = ((T)2 * (xnv[i] + th.v[i] + axv[i] + eev[i] - lh.v[i]) + gv[i]) / (T)3;
+                cv[i] = c;
+                if (ukind == uset::kUsetHalfspace && !xs) av[i] = ua[c];
+              }
+            }
+          }
+          if (ukind != uset::kUsetBox)
+            uset::project_inputs<T, 4>(ukind, ur, av, wv, cv, nx, n, g,
+                                       [](int jj) { return jj >> 2; }, [](int jj) { return jj & 3; });
+          if (mine) {
           const V4<T> lo4 = ld4(sLo + c0), hi4 = ld4(sHi + c0);
           V4<T> oz, ov, ot, ob, ol;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int c = c0 + i;
             if (c < n) {
-              const bool xs = c < nx;
-              const T ax = xs ? ax4.v[i] : x0.v[i];
-              const T bd = xs ? bd4.v[i] : du4.v[i];
-              const T ee = e4.v[i];
-              const T xn = x1.v[i];
-              const T gam = bd + bh.v[i] - ax - ee + lh.v[i];
-              const T w = ((T)2 * (xn + th.v[i] + ax + ee - lh.v[i]) + gam) / (T)3;
-              const T z = clampv(w, lo4.v[i], hi4.v[i]);
+              const T ax = axv[i], bd = bdv[i], ee = eev[i], xn = xnv[i], gam = gv[i];
+              const T z = (c < nx || ukind == uset::kUsetBox) ? clampv(wv[i], lo4.v[i], hi4.v[i])
+                                                              : wv[i];
               const T v = (T)0.5 * (z + gam);
               const T tt = th.v[i] + xn - z;
               const T be = bh.v[i] + bd - v;
@@ -468,6 +494,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           st4(o + 2 * nP, ot);
           st4(o + 3 * nP, ob);
           st4(o + 4 * nP, ol);
+          }
         }
         __syncthreads();
       }

@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(256) resident_kernel(Args<T> a, ResPlan pl) {
   int streak = 0;  // consecutive momentum steps since the last restart
   int momentum = 0, status = kMaxIter, iters = 0;
   double cval = 0.0;
+  double cbest = INFINITY;  // stall test: best c so far, the iteration that set it, and the
+  int itbest = 0, itfirst = -1;  // first iteration with c <= stall_below
   int cur = 0, prv = 2, nw = 1;
   cl.sync();
 
@@ -258,6 +260,10 @@ __global__ void __launch_bounds__(256) resident_kernel(Args<T> a, ResPlan pl) {
         status = kNonFinite; stop = 1;
       } else if (c <= a.eps) {
         status = kConverged; stop = 1;
+      } else if (a.stall_win > 0 && c <= a.stall_below && !(c < a.stall_fac * cbest) &&
+                 (double)(it - itbest) >=
+                     fmax((double)a.stall_win, a.stall_rel * (double)(itfirst < 0 ? it : itfirst))) {
+        status = kStalled; stop = 1;
       } else if (it + 1 >= a.max_iters) {
         status = kMaxIter; stop = 1;
       } else {
@@ -275,6 +281,13 @@ __global__ void __launch_bounds__(256) resident_kernel(Args<T> a, ResPlan pl) {
           coef = 0.0;
         }
         cprev = c;
+      }
+      if (c <= a.stall_below) {
+        if (itfirst < 0) itfirst = it;
+        if (c < a.stall_fac * cbest) {
+          cbest = c;
+          itbest = it;
+        }
       }
       sStop = stop;
       sCoef = coef;

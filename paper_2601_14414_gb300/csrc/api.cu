@@ -53,6 +53,9 @@ int ensure_coef_table(pimpc_solver *s) {
   return PIMPC_OK;
 }
 
+int store_input_sets(pimpc_solver *s, const int *kind, const double *r, const double *a,
+                     cudaStream_t st);
+
 void graph_invalidate(pimpc_solver *s) {
   for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
   s->graphs.clear();
@@ -144,6 +147,10 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   }
   if (sc.family == 2 && (precision != PIMPC_F32 || lti)) {
     why = "halo tiles serve stage-varying FP32 instances";
+    return PIMPC_EINVAL;
+  }
+  if (s->any_uset && sc.family != 0 && sc.family != 5) {
+    why = "non-box input sets need schedule family 0 or 5";
     return PIMPC_EINVAL;
   }
   if (sc.ctas_per_sm < 0 || sc.ctas_per_sm > 8 || sc.item_scale < 0 || sc.item_scale > 64) {
@@ -562,6 +569,16 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.warm = warm_start;
   a.ferr = s->ferr;
   a.bar_limit = s->bar_limit;
+  a.stall_win = s->stall_win;
+  a.uset_kind = s->any_uset ? s->uset_kind_d : nullptr;
+  a.uset_r = s->any_uset ? s->uset_r_T : nullptr;
+  a.uset_a = s->any_uset ? s->uset_a_T : nullptr;
+  a.stall_fac = s->stall_fac;
+  a.stall_below = s->stall_below;
+  a.stall_rel = s->stall_rel;
+  a.itfirst = s->itfirst;
+  a.cbest = s->cbest;
+  a.itbest = s->itbest;
   a.u_out = u_dev;
   a.x_out = x_dev;
   a.coef_tab = s->coef_tab;
@@ -615,6 +632,11 @@ int prepare_polish(pimpc_solver *s, cudaStream_t st) {
                                     sh->blk_T, sh->ferr, st),
                 "polish factorise");
     s->shadow_fgen = s->fgen;
+  }
+  if (s->any_uset != sh->any_uset || s->any_uset) {
+    const int rc = store_input_sets(sh, s->uset_kind_h.data(), s->uset_r_h.data(),
+                                    s->uset_a_h.data(), st);
+    if (rc != PIMPC_OK) return fail(s, rc, std::string("polish input sets: ") + sh->err);
   }
   sh->stale = false;
   sh->solved = true;
@@ -726,6 +748,9 @@ void pimpc_destroy(pimpc_solver *s) {
   graph_invalidate(s);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->mask_alloc) cudaFree(s->mask_alloc);
+  if (s->uset_kind_d) cudaFree(s->uset_kind_d);
+  if (s->uset_r_T) cudaFree(s->uset_r_T);
+  if (s->uset_a_T) cudaFree(s->uset_a_T);
   delete s;
 }
 
@@ -827,6 +852,9 @@ int pimpc_create(int batch, const int *nx, const int *nu, const int *N, int lti,
   chk(dalloc(s, &s->cprev, sizeof(double) * batch));
   chk(dalloc(s, &s->coef, sizeof(double) * batch));
   chk(dalloc(s, &s->cacc, sizeof(double) * batch));
+  chk(dalloc(s, &s->cbest, sizeof(double) * batch));
+  chk(dalloc(s, &s->itbest, sizeof(int) * batch));
+  chk(dalloc(s, &s->itfirst, sizeof(int) * batch));
   chk(dalloc(s, &s->ndone, sizeof(int) * batch));
   chk(dalloc(s, &s->stop, sizeof(int) * batch));
   chk(dalloc(s, &s->nitems_inst, sizeof(int) * 2 * batch));
@@ -1170,6 +1198,97 @@ int pimpc_set_restart_mask(pimpc_solver *s, const unsigned char *mask, int len, 
   if (mem == PIMPC_HOST) PIMPC_CHECK(s, cudaStreamSynchronize(st), "mask");
   s->mask = buf;
   s->mask_len = len;
+  return PIMPC_OK;
+}
+
+}  // extern "C"
+
+namespace pimpc {
+// Input sets from host arrays (validated): kind [batch], r [batch], a [sum nu] (may be null).
+int store_input_sets(pimpc_solver *s, const int *kind, const double *r, const double *a,
+                     cudaStream_t st) {
+  bool any = false;
+  for (int j = 0; j < s->batch; ++j) {
+    const int k = kind[j];
+    if (k < 0 || k > 4) return fail(s, PIMPC_EINVAL, "input set kind must be 0..4");
+    if (k == 0) continue;
+    any = true;
+    if (!std::isfinite(r[j]) || ((k == 1 || k == 2) && r[j] < 0.0))
+      return fail(s, PIMPC_EINVAL, "input set: r must be finite (and >= 0 for a ball)");
+    if (k == 3) {
+      if (!a) return fail(s, PIMPC_EINVAL, "halfspace input set needs its normal a");
+      double nn = 0.0;
+      for (int i = 0; i < s->nu[j]; ++i) {
+        const double v = a[s->off_nu[j] + i];
+        if (!std::isfinite(v)) return fail(s, PIMPC_EINVAL, "input set: non-finite normal");
+        nn += v * v;
+      }
+      if (!(nn > 0.0)) return fail(s, PIMPC_EINVAL, "input set: zero halfspace normal");
+    }
+  }
+  if (any && s->sched.family != 0 && s->sched.family != 5)
+    return fail(s, PIMPC_EINVAL, "non-box input sets need schedule family 0 or 5");
+  const size_t ts = s->prec == PIMPC_F32 ? 4 : 8;
+  if (!s->uset_kind_d) {
+    cudaError_t e = cudaMalloc((void **)&s->uset_kind_d, sizeof(int) * s->batch);
+    if (e == cudaSuccess) e = cudaMalloc(&s->uset_r_T, ts * s->batch);
+    if (e == cudaSuccess) e = cudaMalloc(&s->uset_a_T, ts * s->tot_n);
+    if (e != cudaSuccess) return fail(s, PIMPC_ENOMEM, "input set arrays");
+  }
+  s->uset_kind_h.assign(kind, kind + s->batch);
+  s->uset_r_h.assign(r, r + s->batch);
+  if (a) s->uset_a_h.assign(a, a + s->tot_nu);
+  else s->uset_a_h.assign(s->tot_nu, 0.0);
+  PIMPC_CHECK(s, cudaMemcpyAsync(s->uset_kind_d, s->uset_kind_h.data(), sizeof(int) * s->batch,
+                                 cudaMemcpyHostToDevice, st), "input set kinds");
+  double *tmp = nullptr;  // FP64 staging for the conversion, freed before returning
+  PIMPC_CHECK(s, cudaMalloc((void **)&tmp, sizeof(double) * (s->batch + s->tot_nu)),
+              "input set staging");
+  PIMPC_CHECK(s, cudaMemcpyAsync(tmp, s->uset_r_h.data(), sizeof(double) * s->batch,
+                                 cudaMemcpyHostToDevice, st), "input set radii");
+  PIMPC_CHECK(s, cudaMemcpyAsync(tmp + s->batch, s->uset_a_h.data(), sizeof(double) * s->tot_nu,
+                                 cudaMemcpyHostToDevice, st), "input set normals");
+  PIMPC_CHECK(s, launch_convert(tmp, s->batch, s->prec, s->uset_r_T, st), "input set radii");
+  PIMPC_CHECK(s, launch_gather_n(s->L, nullptr, tmp + s->batch, s->tot_n, s->prec, s->uset_a_T, st),
+              "input set normals");
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFree(tmp);
+  PIMPC_CHECK(s, e2, "input sets");
+  s->any_uset = any;
+  graph_invalidate(s);
+  return PIMPC_OK;
+}
+}  // namespace pimpc
+
+extern "C" {
+
+int pimpc_set_input_set(pimpc_solver *s, const int *kind, const double *r, const double *a,
+                        int mem, void *stream) {
+  if (!s || !kind || !r) return fail(s, PIMPC_EINVAL, "kind and r are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(s->device);
+  if (mem == PIMPC_HOST) return store_input_sets(s, kind, r, a, st);
+  // device arrays: validated on host copies (a setup call, not on the solve path)
+  std::vector<int> kh(s->batch);
+  std::vector<double> rh(s->batch), ah(a ? s->tot_nu : 0);
+  PIMPC_CHECK(s, cudaMemcpyAsync(kh.data(), kind, sizeof(int) * s->batch, cudaMemcpyDeviceToHost, st), "copy kinds");
+  PIMPC_CHECK(s, cudaMemcpyAsync(rh.data(), r, sizeof(double) * s->batch, cudaMemcpyDeviceToHost, st), "copy r");
+  if (a) PIMPC_CHECK(s, cudaMemcpyAsync(ah.data(), a, sizeof(double) * s->tot_nu, cudaMemcpyDeviceToHost, st), "copy a");
+  PIMPC_CHECK(s, cudaStreamSynchronize(st), "input sets");
+  return store_input_sets(s, kh.data(), rh.data(), a ? ah.data() : nullptr, st);
+}
+
+int pimpc_set_stall(pimpc_solver *s, int window, double factor, double below, double rel) {
+  if (!s) return PIMPC_EINVAL;
+  if (window < 0) return fail(s, PIMPC_EINVAL, "window must be >= 0");
+  if (!(factor > 0.0 && factor <= 1.0)) return fail(s, PIMPC_EINVAL, "factor must be in (0, 1]");
+  if (!(below >= 0.0)) return fail(s, PIMPC_EINVAL, "below must be >= 0");
+  if (!(rel >= 0.0) || !std::isfinite(rel)) return fail(s, PIMPC_EINVAL, "rel must be >= 0");
+  graph_invalidate(s);
+  s->stall_win = window;
+  s->stall_fac = factor;
+  s->stall_below = below;
+  s->stall_rel = rel;
   return PIMPC_OK;
 }
 

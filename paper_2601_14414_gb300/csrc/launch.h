@@ -39,6 +39,16 @@ struct AdmmLaunch {
   const int *grp;   // blocked kernel: lane groups per sub-chunk of each instance
   int warm;
   const int *ferr;  // [batch] nonzero: the instance's factorisation met a non-positive pivot
+  // input sets (null: the box for every instance): kind [batch], r [batch], a [sum n] (type T)
+  const int *uset_kind;
+  const void *uset_r, *uset_a;
+  // stop at the arithmetic's floor: once c <= stall_below (first at iteration i0), no c below
+  // stall_fac x the best c for max(stall_win, stall_rel x i0) iterations
+  int stall_win;    // 0: off (Algorithm 1's stop test only)
+  double stall_fac, stall_below, stall_rel;
+  double *cbest;    // [batch] best c so far, and the iteration that set it
+  int *itbest;
+  int *itfirst;     // [batch] i0 (-1: c not yet below stall_below)
   int bar_limit;    // grid-barrier polls before giving up (0: the default limit)
   // launch shape and shared-memory plan (elements of the iteration type)
   int grid, threads;

@@ -42,6 +42,12 @@ struct Args {
   const double *coef_tab;  // momentum factor of the m-th consecutive momentum step (resident)
   const int *grp;          // blocked kernel: lane groups per sub-chunk of each instance
   const int *ferr;         // [batch] factorisation failure flags (may be null)
+  int stall_win;           // > 0: stop an instance whose c has stalled (see stalled())
+  const int *uset_kind;    // input set of each instance (null: all boxes), radius, normal
+  const T *uset_r, *uset_a;
+  double stall_fac, stall_below, stall_rel;
+  double *cbest;
+  int *itbest, *itfirst;
 };
 
 // Iterate element (vector b in {z, v, theta, beta, lambda}, component c) of stage k (its own
@@ -96,6 +102,25 @@ __device__ inline bool grid_sync(Ctl *c, unsigned nblocks, int *sOk) {
   return *sOk != 0;
 }
 
+// The floor of the iteration's arithmetic: since c^{i+1} first came below stall_below (at
+// iteration i0), it has not fallen below stall_fac times the best c for max(stall_win,
+// stall_rel i0) iterations. In FP32 c stops decreasing once the rounding of the iterates
+// dominates their change; plateaus of the accelerated iteration far above that floor do not
+// count, and the window grows with i0 because an instance that converges slowly (large i0)
+// keeps improving its iterates for longer after its c has levelled off. Updates the best c.
+// Called by one thread, only for c <= stall_below.
+template <typename T>
+__device__ inline bool stalled(const Args<T> &a, int j, int it, double c) {
+  if (a.itfirst[j] < 0) a.itfirst[j] = it;
+  if (c < a.stall_fac * a.cbest[j]) {
+    a.cbest[j] = c;
+    a.itbest[j] = it;
+    return false;
+  }
+  const double win = fmax((double)a.stall_win, a.stall_rel * (double)a.itfirst[j]);
+  return (double)(it - a.itbest[j]) >= win;
+}
+
 // Step 4's reduction is finished by the caller; this adds the item's share of c^{i+1} and, for
 // the instance's last item of the iteration, applies steps 5-7. Called by one thread.
 template <typename T>
@@ -117,6 +142,8 @@ __device__ inline void finish_item(const Args<T> &a, int j, int it, double part)
     st.status = kNonFinite; stop = 1;
   } else if (c <= a.eps) {
     st.status = kConverged; stop = 1;
+  } else if (a.stall_win > 0 && c <= a.stall_below && stalled(a, j, it, c)) {
+    st.status = kStalled; stop = 1;
   } else if (it + 1 >= a.max_iters) {
     st.status = kMaxIter; stop = 1;
   } else {
@@ -196,6 +223,11 @@ __global__ void solve_init_kernel(Args<T> a, int warm) {
     a.cacc[j] = 0.0;
     a.ndone[j] = 0;
     a.stop[j] = a.max_iters <= 0 ? 1 : 0;
+    if (a.stall_win > 0) {
+      a.cbest[j] = INFINITY;
+      a.itbest[j] = 0;
+      a.itfirst[j] = -1;
+    }
     InstState s;
     s.iters = 0; s.status = kMaxIter; s.momentum = 0; s.pad = 0; s.c = 0.0;
     a.st[j] = s;
@@ -286,6 +318,16 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.coef_tab = s.coef_tab;
   a.grp = s.grp;
   a.ferr = s.ferr;
+  a.stall_win = s.stall_win;
+  a.uset_kind = s.uset_kind;
+  a.uset_r = (const T *)s.uset_r;
+  a.uset_a = (const T *)s.uset_a;
+  a.stall_fac = s.stall_fac;
+  a.stall_below = s.stall_below;
+  a.stall_rel = s.stall_rel;
+  a.itfirst = s.itfirst;
+  a.cbest = s.cbest;
+  a.itbest = s.itbest;
   return a;
 }
 

@@ -27,6 +27,7 @@ constexpr int kMaxIter = 1;
 constexpr int kNonFinite = 2;
 constexpr int kTimeout = 3;
 constexpr int kFactorFailed = 4;
+constexpr int kStalled = 5;
 constexpr int kMaxNLtv = 32;
 constexpr int kMaxNLti = 64;
 

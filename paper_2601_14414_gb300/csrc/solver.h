@@ -39,6 +39,18 @@ struct pimpc_solver {
   unsigned char *mask = nullptr, *mask_alloc = nullptr;
   int mask_len = 0;
   int bar_limit = 0;  // grid-barrier polls before a launch gives up (0: the built-in limit)
+  int stall_win = 0;  // stall stop: window (0: off) and factor, per-instance best c / iteration
+  double stall_fac = 0.5, stall_below = 1e-9, stall_rel = 0.0;
+  int *itfirst = nullptr;
+  double *cbest = nullptr;
+  int *itbest = nullptr;
+  // input sets (pimpc_set_input_set): device kind [batch], r [batch] and normal [sum n] in the
+  // iteration precision (x slots 0), allocated by the first call; host copies for the polish
+  bool any_uset = false;
+  int *uset_kind_d = nullptr;
+  void *uset_r_T = nullptr, *uset_a_T = nullptr;
+  std::vector<int> uset_kind_h;
+  std::vector<double> uset_r_h, uset_a_h;  // r [batch], a [sum nu]
   int nitems = 0;
   // options and state
   double rho = 1.0, eps = 1e-6, eta = 0.999;

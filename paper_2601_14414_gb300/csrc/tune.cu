@@ -89,9 +89,11 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
   // Trial solves: zero state, no reference, a fixed number of iterations.
   const double eps = s->eps;
   const int max_iters = s->max_iters;
+  const int stall_win = s->stall_win;
   const Schedule old = s->sched;
   s->eps = -1.0;
   s->max_iters = trial_iters;
+  s->stall_win = 0;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -123,6 +125,7 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
   cudaEventDestroy(e1);
   s->eps = eps;
   s->max_iters = max_iters;
+  s->stall_win = stall_win;
   std::string why;
   const int rc2 = apply_schedule(s, rc == PIMPC_OK ? pick : old, why);
   if (rc != PIMPC_OK) return rc;

@@ -19,7 +19,8 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, 1, 2, 3, 4
-CONVERGED, MAXITER, NONFINITE, TIMEOUT, FACTOR_FAILED = 0, 1, 2, 3, 4
+CONVERGED, MAXITER, NONFINITE, TIMEOUT, FACTOR_FAILED, STALLED = 0, 1, 2, 3, 4, 5
+USET_BOX, USET_BALL2, USET_BALL1, USET_HALFSPACE, USET_SOC = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 HOST, DEVICE = 0, 1
 MODEL_QUADROTOR, MODEL_CARTPOLE, MODEL_CSTR = 0, 1, 2
@@ -46,6 +47,8 @@ _SIGS = {
     "pimpc_get_stats": (_I, [_VP, _VP, _VP, _VP, _VP, _I, _VP]),
     "pimpc_set_restart_mask": (_I, [_VP, _VP, _I, _I, _VP]),
     "pimpc_set_wait_limit": (_I, [_VP, _I]),
+    "pimpc_set_stall": (_I, [_VP, _I, _D, _D, _D]),
+    "pimpc_set_input_set": (_I, [_VP, _VP, _VP, _VP, _I, _VP]),
     "pimpc_plant_step": (_I, [_VP, _I, _VP, _D, _VP, _VP, _VP, _I, _VP]),
     "pimpc_backward": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP]),
     "pimpc_solve_static": (_I, [_I, _I, _I, _I] + [_VP] * 11 + [_D, _D, _I, _I, _D] + [_VP] * 6),
@@ -203,6 +206,18 @@ def pimpc_get_stats(h, iters=None, c=None, status=None, momentum_iters=None):
     _check(h, load().pimpc_get_stats(h, *p, mem, st))
 
 
+def pimpc_set_input_set(h, kind, r, a=None):
+    """kind: int [batch] (numpy host array or int32 CUDA tensor), r [batch], a [sum nu] or None."""
+    if not _is_torch(kind):
+        kind = np.ascontiguousarray(kind, dtype=np.int32)
+    p, mem, st = _marshal(kind, r, a)
+    _check(h, load().pimpc_set_input_set(h, *p, mem, st))
+
+
+def pimpc_set_stall(h, window, factor=0.5, below=1e-9, rel=0.0):
+    _check(h, load().pimpc_set_stall(h, int(window), float(factor), float(below), float(rel)))
+
+
 def pimpc_set_wait_limit(h, polls):
     _check(h, load().pimpc_set_wait_limit(h, int(polls)))
 
@@ -319,6 +334,12 @@ def pack(instances):
         out["ref"] = _cat([i["ref"] for i in instances])
     out["ref_per_stage"] = per_stage
     out["rho"] = float(instances[0]["rho"])
+    if any(i.get("uset") is not None for i in instances):
+        us = [i.get("uset") or dict(kind=USET_BOX, r=0.0) for i in instances]
+        out["uset_kind"] = np.array([u["kind"] for u in us], np.int32)
+        out["uset_r"] = np.array([float(u.get("r", 0.0)) for u in us])
+        out["uset_a"] = _cat([np.zeros(i["nu"]) if u.get("a") is None else u["a"]
+                              for i, u in zip(instances, us)])
     return out
 
 
@@ -344,6 +365,8 @@ class Solver:
         pimpc_set_options(self.h, self.p["rho"], eps, max_iters, accel, eta)
         if "A" in self.p:
             pimpc_set_dynamics(self.h, self.p["A"], self.p["B"], self.p["e"])
+        if "uset_kind" in self.p:
+            pimpc_set_input_set(self.h, self.p["uset_kind"], self.p["uset_r"], self.p["uset_a"])
 
     def close(self):
         if self.h is not None:
