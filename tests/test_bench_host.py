@@ -4,7 +4,8 @@
   and the iterates read and written, plus the previous iterate on momentum iterations — checked
   against the sum written out by hand for small sizes.
 * The profiled traffic: the DRAM bytes per algorithmic byte of the committed ncu summary are used
-  only while the summary's source hash matches the kernel source; a stale summary gives None.
+  only while the summary's source hash matches the kernel source and the headers compiled into
+  it; a stale summary gives None.
 """
 import hashlib
 import os
@@ -35,12 +36,20 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     src = csrc / "admm_blk.cu"
     src.write_text("// kernel source\n")
-    digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    h = hashlib.sha256(src.read_bytes())
+    for name in bench.KERNEL_HEADERS:                     # headers compiled into the kernel
+        (csrc / name).write_text(f"// {name}\n")
+        h.update((csrc / name).read_bytes())
+    digest = h.hexdigest()[:16]
     prof = tmp_path / "profiles" / "blk_kernel_f32_batched_512x30.md"
     prof.write_text(f"traffic_per_algorithmic_byte: 1.2345\n\nadmm_blk.cu sha256[:16]: {digest} (x)\n")
     monkeypatch.setattr(bench, "HERE", str(tmp_path))
     assert bench.profiled_traffic(5) == 1.2345
     assert bench.profiled_traffic(7) is None            # no summary for that family
+    (csrc / "lockstep.cuh").write_text("// changed\n")    # a header changed since the capture
+    assert bench.profiled_traffic(5) is None
+    (csrc / "lockstep.cuh").write_text("// lockstep.cuh\n")
+    assert bench.profiled_traffic(5) == 1.2345
     src.write_text("// kernel source, changed\n")        # the kernel changed since the capture
     assert bench.profiled_traffic(5) is None
 
