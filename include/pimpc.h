@@ -325,7 +325,11 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
  *                   products of blocks of stages as dense matrix-matrix contractions; 5: a
  *                   group of 4, 8 or 16 lanes per stage on blocked stage blocks, four
  *                   components per lane (every precision and instance kind; the default for
- *                   FP32 iterations); -1: the default.
+ *                   FP32 iterations); 6: stage-invariant instances with FP32 iterations, the
+ *                   per-stage products of 127-stage tiles as matrix products on the tensor
+ *                   cores (tcgen05, TF32 operands split in two for FP32 accuracy; nx and nu
+ *                   rounded up to 16 must sum to 64 or less, nu's at most nx's); -1: the
+ *                   default.
  *   ctas_per_sm  families 2, 4 and 5: CTAs per SM the shared-memory budget of a CTA is sized
  *                for (0 = 2 for family 2, 1 for family 4; for family 5 the one of 3, 2, 1 that
  *                fits every instance with the most stages in flight); ignored by families 0
@@ -336,7 +340,8 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
  *                this many tiles per work item (0 = 4); family 3: CTAs per instance, 1, 2, 4,
  *                8 or 16 (0 = the fewest whose shared memory holds the instance, or the most
  *                that leave each CTA four stages when the batch occupies few SMs); family 4:
- *                stages per block (0 = as many as the shared memory holds, at most 128).
+ *                stages per block (0 = as many as the shared memory holds, at most 128);
+ *                family 6: 127-stage tiles per work item (0 = 2).
  * pimpc_set_schedule re-lays out the stage data and the iterates: the next solve factorises
  * again and starts cold (warm_start is treated as 0 until one solve has run).
  * Errors: PIMPC_EINVAL (a bad value, or an instance that does not fit the schedule; the

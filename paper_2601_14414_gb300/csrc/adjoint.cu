@@ -501,7 +501,8 @@ extern "C" int pimpc_backward(pimpc_solver *s, const double *dL_du, const double
   if (s->last_warm != 0 || s->last_accel != 0 || s->last_eps >= 0.0)
     return fail(s, PIMPC_ESTATE,
                 "the last solve must use warm_start = 0, accel = 0 and eps < 0 (fixed iterations)");
-  if (s->tiled == 1) return fail(s, PIMPC_ESTATE, "the adjoint does not read the 32-stage tiled layout");
+  if (s->tiled == 1 || s->tiled == 4)
+    return fail(s, PIMPC_ESTATE, "the adjoint does not read the tiled iterate layouts (schedules 6 and the static entry point)");
   if (s->any_uset) return fail(s, PIMPC_ESTATE, "the adjoint covers box input sets only");
   cudaStream_t st = (cudaStream_t)stream;
   cudaSetDevice(s->device);

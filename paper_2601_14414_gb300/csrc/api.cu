@@ -137,9 +137,22 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   // pipe bounds those, and the 4-wide padding of the blocked layout adds FP64 work); the other
   // families are chosen explicitly or by the autotuner.
   if (sc.family < 0) sc.family = precision == PIMPC_F32 ? 5 : 0;
-  if (sc.family != 0 && sc.family != 2 && sc.family != 3 && sc.family != 4 && sc.family != 5) {
-    why = "schedule family must be 0, 2, 3, 4 or 5";
+  if (sc.family != 0 && sc.family != 2 && sc.family != 3 && sc.family != 4 && sc.family != 5 &&
+      sc.family != 6) {
+    why = "schedule family must be 0, 2, 3, 4, 5 or 6";
     return PIMPC_EINVAL;
+  }
+  if (sc.family == 6) {
+    if (!lti || precision != PIMPC_F32) {
+      why = "the tensor-core schedule serves stage-invariant instances with FP32 iterations";
+      return PIMPC_EINVAL;
+    }
+    for (int j = 0; j < batch; ++j)
+      if (!tc_fits(nx[j], nu[j])) {
+        why = "the tensor-core schedule needs nx and nu rounded up to 16 to sum to at most 64 "
+              "(and nu's to be at most nx's)";
+        return PIMPC_EINVAL;
+      }
   }
   if (sc.family == 4 && !lti) {
     why = "the contraction schedule serves stage-invariant instances";
@@ -159,7 +172,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   }
   // halo tiles and the blocked lane groups have layouts of their own; the resident and the
   // contraction families read the plain layout
-  const int tiled = sc.family == 2 ? 2 : (sc.family == 5 ? 3 : 0);
+  const int tiled = sc.family == 2 ? 2 : (sc.family == 5 ? 3 : (sc.family == 6 ? 4 : 0));
   s->tiled = tiled;
   int nsm = 0, smem_sm = 0, optin = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
@@ -186,7 +199,43 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   int bps = 0;
   cudaError_t e = cudaSuccess;
-  if (sc.family == 4) {
+  std::vector<int64_t> tc_off(batch, 0);
+  int64_t tot_tc = 0;
+  if (sc.family == 6) {
+    // Tiles of 127 stages (128 MMA rows with the stage before the tile); items of a few tiles
+    // so that an instance's matrices are copied to shared memory once per item.
+    const int tpi = sc.item_scale > 0 ? sc.item_scale : 2;
+    size_t smem = 0;
+    for (int j = 0; j < batch; ++j) {
+      const int n = nx[j] + nu[j];
+      W[j] = block_words(nx[j], nu[j]);
+      blk[j] = tot_blk;
+      tot_blk += ((int64_t)blocks_per_instance(lti, N[j]) * W[j] + 31) / 32 * 32;
+      Ni[j] = tot_Ni;
+      const int np = ((nx[j] + 15) & ~15) + ((nu[j] + 15) & ~15);
+      tot_Ni += ((int64_t)(N[j] + 127) / 128 * 128 * 5 * np + 31) / 32 * 32;
+      tc_off[j] = tot_tc;
+      tot_tc += tc_block_words(nx[j], nu[j]);
+      smem = std::max(smem, tc_smem_bytes(nx[j], nu[j]));
+    }
+    if (smem + 1024 > (size_t)optin) {
+      why = "the tensor-core schedule needs more shared memory than one CTA has";
+      return PIMPC_EINVAL;
+    }
+    for (int oi = 0; oi < batch; ++oi) {
+      const int j = order[oi];
+      for (int a0 = 0; a0 < N[j]; a0 += 127 * tpi) {
+        item_inst.push_back(j);
+        item_a.push_back(a0);
+        item_b.push_back(std::min(N[j], a0 + 127 * tpi));
+        nitems_inst[j] += 1;
+      }
+    }
+    P.threads = tc_threads();
+    s->smem_admm = smem;
+    e = tc_configure(smem, &bps);
+    bps = std::min(bps, 1);
+  } else if (sc.family == 4) {
     // Blocks of LB stages (LB from the shared-memory budget of cps CTAs per SM); an item holds
     // several consecutive blocks, so the instance's matrices are expanded once per item.
     const int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 1;
@@ -486,6 +535,12 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(lalloc(s, &d_W, sizeof(int) * batch));
   chk(lalloc(s, &d_tw, sizeof(int) * batch));
   chk(lalloc(s, &d_grp, sizeof(int) * batch));
+  s->tc_mat = nullptr;
+  s->tc_off = nullptr;
+  if (sc.family == 6) {
+    chk(lalloc(s, &s->tc_mat, sizeof(float) * (size_t)tot_tc));
+    chk(lalloc(s, &s->tc_off, sizeof(int64_t) * batch));
+  }
   if (e != cudaSuccess) {
     why = std::string("device allocation failed: ") + cudaGetErrorString(e);
     const bool oom = e == cudaErrorMemoryAllocation;
@@ -502,6 +557,8 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(cudaMemcpy(d_W, W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_tw, tw.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_grp, grp.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
+  if (sc.family == 6)
+    chk(cudaMemcpy(s->tc_off, tc_off.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemset(s->blk_T, 0, ts * tot_blk));
   for (int b = 0; b < 3; ++b) chk(cudaMemset(s->it[b], 0, ts * tot_Ni));
   chk(cudaMemset(s->base, 0, sizeof(int) * batch));
@@ -588,6 +645,7 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
                  : s->tiled == 3 ? launch_blk(a, s->prec, s->smem_admm, st)
                  : s->sched.family == 3 ? launch_resident(a, s->prec, s->res_plan, s->smem_admm, st)
                  : s->sched.family == 4 ? launch_gemm(a, s->prec, s->gemm_plan, st)
+                 : s->sched.family == 6 ? launch_tc(a, s->tc_mat, s->tc_off, s->smem_admm, st)
                                         : launch_admm(a, s->prec, st),
               "solve");
   s->solved = true;

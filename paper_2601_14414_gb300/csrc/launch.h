@@ -90,6 +90,15 @@ int64_t blk_region_words(int nx, int nu, int lti, int precision, int S);
 cudaError_t blk_configure(int precision, size_t smem, int *blocks_per_sm);
 cudaError_t launch_blk(const AdmmLaunch &a, int precision, size_t smem, cudaStream_t stream);
 
+// Stage-invariant FP32 instances with the stage products on the tensor cores (tiled == 4).
+int tc_threads();
+bool tc_fits(int nx, int nu);
+int64_t tc_block_words(int nx, int nu);
+size_t tc_smem_bytes(int nx, int nu);
+cudaError_t tc_configure(size_t smem, int *blocks_per_sm);
+cudaError_t launch_tc(const AdmmLaunch &s, const float *tcm, const int64_t *tc_off, size_t smem,
+                      cudaStream_t stream);
+
 // Schedule of the batched solve: which kernel family and how its work is cut.
 struct Schedule {
   int family = -1;       // 0: lane groups on plain stage blocks; 2: one thread per stage on halo
@@ -97,7 +106,9 @@ struct Schedule {
                          // shared memory of one CTA or a cluster (item_scale = CTAs per
                          // instance, 0: the fewest that fit); 4: stage-invariant instances as
                          // dense contractions over blocks of stages; 5: lane groups owning
-                         // 4-column blocks on blocked stage blocks; -1: the default
+                         // 4-column blocks on blocked stage blocks; 6: stage-invariant FP32
+                         // instances with the stage products on the tensor cores; -1: the
+                         // default
   int ctas_per_sm = 0;   // halo tiles and blocked lane groups: CTAs per SM the shared-memory
                          // budget is sized for (0: 2 for halo tiles, 3 for blocked lane groups)
   int item_scale = 0;    // lane groups: sub-chunks per item (0: automatic);

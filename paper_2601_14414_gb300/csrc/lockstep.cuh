@@ -54,7 +54,10 @@ struct Args {
 // copy). Plain layout: stage-major with stride n5p. Tiled layout: tiles of 32 stages,
 // element-major inside a tile (one 128-byte line per element for 32 stages in FP32). Halo
 // tiles: tw slots per tile (see pimpc_internal.cuh). Blocked layout: stage-major, every vector
-// padded to a multiple of 4 (n5p is not used).
+// padded to a multiple of 4 (n5p is not used). Layout 4 (tensor-core schedule): tiles of 128
+// stages; inside a tile, for every vector and every group of 4 components of the padded vector
+// (x part and u part each rounded up to 16), the 128 stages' 4 components contiguous (one
+// 16-byte load per stage); tw passes nx for it (layout_aux).
 __host__ __device__ inline int64_t iter_index(int tiled, int tw, int n, int n5p, int k, int b,
                                               int c) {
   if (tiled == 1) return (int64_t)(k >> 5) * (32 * 5 * n) + (int64_t)(b * n + c) * 32 + (k & 31);
@@ -64,7 +67,19 @@ __host__ __device__ inline int64_t iter_index(int tiled, int tw, int n, int n5p,
     return (int64_t)t * tile_iter_words(tw, n) + (int64_t)(b * n + c) * tw + s;
   }
   if (tiled == 3) return (int64_t)k * bl_rec(n) + b * bl_pad4(n) + c;
+  if (tiled == 4) {  // tw carries nx here: vectors padded to (nx, nu) rounded up to 16 each
+    const int nx = tw, nxp = (nx + 15) & ~15, np = nxp + ((n - nx + 15) & ~15);
+    const int p = c < nx ? c : nxp + (c - nx);
+    return (int64_t)(k >> 7) * (128 * 5 * np) + (int64_t)(b * np + (p & ~3)) * 128 + (k & 127) * 4 +
+           (p & 3);
+  }
   return (int64_t)k * n5p + b * n + c;
+}
+
+// The per-instance parameter iter_index takes besides n: the halo tile width (layout 2) or nx
+// (layout 4).
+__host__ __device__ inline int layout_aux(const Layout &L, int j) {
+  return L.tiled == 2 ? L.tw[j] : (L.tiled == 4 ? L.nx[j] : 0);
 }
 
 __host__ __device__ inline int iter_stride_plain(int n, int tsize) {
@@ -241,7 +256,7 @@ __global__ void prepare_kernel(Args<T> a, int warm, const int *old_base) {
   const int j = blockIdx.y;
   const int n = a.L.nx[j] + a.L.nu[j], N = a.L.N[j];
   const int tiled = a.L.tiled;
-  const int tw = tiled == 2 ? a.L.tw[j] : 0;
+  const int tw = layout_aux(a.L, j);
   const int n5p = iter_stride_plain(n, (int)sizeof(T));
   const int64_t ib = a.L.Ni[j];
   T *dst = a.it[a.base[j]] + ib;
@@ -281,7 +296,7 @@ __global__ void output_kernel(Args<T> a, double *u_out, double *x_out) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
-    const int tw = a.L.tiled == 2 ? a.L.tw[j] : 0;
+    const int tw = layout_aux(a.L, j);
     const double v = (double)z[iter_index(a.L.tiled, tw, n, n5p, k, 0, c)];
     if (c < nx) {
       if (x_out) x_out[a.L.Nnx[j] + (int64_t)k * nx + c] = v;

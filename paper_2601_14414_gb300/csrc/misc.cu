@@ -37,7 +37,7 @@ __global__ void export_kernel(Layout L, T *it0, T *it1, T *it2, const int *base,
   T *bufs[3] = {it0, it1, it2};
   const T *src = bufs[base[j]] + L.Ni[j];
   double *outs[5] = {z, v, th, be, la};
-  const int tw = L.tiled == 2 ? L.tw[j] : 0;
+  const int tw = ls::layout_aux(L, j);
   for (int64_t t = threadIdx.x; t < (int64_t)N * n; t += blockDim.x) {
     const int k = (int)(t / n), c = (int)(t - (int64_t)k * n);
     for (int b = 0; b < 5; ++b)
@@ -118,7 +118,7 @@ __global__ void copy_iterates_kernel(Layout Ls, const S *s0, const S *s1, const 
   const S *src = srcs[base_s[j]] + Ls.Ni[j];
   double *dst = dsts[base_d[j]] + Ld.Ni[j];
   const int n5s = ls::iter_stride_plain(n, (int)sizeof(S)), n5d = ls::iter_stride_plain(n, 8);
-  const int tws = Ls.tiled == 2 ? Ls.tw[j] : 0;
+  const int tws = ls::layout_aux(Ls, j);
   for (int64_t t = threadIdx.x; t < (int64_t)N * 5 * n; t += blockDim.x) {
     const int k = (int)(t / (5 * n)), r = (int)(t - (int64_t)k * 5 * n);
     const int b = r / n, c = r - b * n;

@@ -42,6 +42,8 @@ struct pimpc_solver {
   int stall_win = 0;  // stall stop: window (0: off) and factor, per-instance best c / iteration
   double stall_fac = 0.5, stall_below = 1e-9, stall_rel = 0.0;
   int *itfirst = nullptr;
+  float *tc_mat = nullptr;       // tensor-core schedule: per-instance matrix blocks
+  int64_t *tc_off = nullptr;     // [batch] word offsets of those blocks
   double *cbest = nullptr;
   int *itbest = nullptr;
   // input sets (pimpc_set_input_set): device kind [batch], r [batch] and normal [sum n] in the
