@@ -54,6 +54,11 @@ def parse_args():
                          "e2e or CPU legs; prints the algorithmic bytes of the solve launch")
     ap.add_argument("--fixed-iters", type=int, default=None,
                     help="with --profile: run exactly this many iterations (eps < 0)")
+    ap.add_argument("--profile-workload", choices=["batched", "large_lti"], default="batched",
+                    help="with --profile: the batched uneven workload, or the large-state LTI one "
+                         "(plain iterations)")
+    ap.add_argument("--family", type=int, default=-1,
+                    help="with --profile: the schedule family of the solve (-1: the default)")
     return ap.parse_args()
 
 
@@ -181,7 +186,8 @@ SOLVE_KERNELS = {
     5: ("blk_kernel<float>", "admm_blk.cu", "blk_kernel_f32_batched_512x30.md"),
 }
 # Headers compiled into every solve kernel: a change there changes the kernel too.
-KERNEL_HEADERS = ("lockstep.cuh", "bulk.cuh", "products.cuh", "pimpc_internal.cuh", "launch.h")
+KERNEL_HEADERS = ("lockstep.cuh", "bulk.cuh", "products.cuh", "pimpc_internal.cuh", "launch.h",
+                  "usets.cuh", "tc.cuh")
 
 
 def kernel_source_hash(source):
@@ -502,39 +508,98 @@ def bench_afti16(pimpc, W, precision, family=None):
                 max_abs_y1=float(np.abs(xs[1:, 1]).max()), paper_mean_iterations=2030)
 
 
-def bench_large_lti(torch, pimpc, W, iters=400):
-    """256 LTI instances, nx 48, nu 16, N 1000 (bounds active on about a fifth of the inputs):
-    a fixed number of accelerated iterations in FP32 and in FP64 (convergence to c <= 1e-10 takes
-    about 20000 iterations here, beyond a benchmark's minutes); time per iteration, iterate
-    traffic and the FP32 vs FP64 difference after the same iterations."""
+def bench_large_lti(torch, pimpc, W, iters=200):
+    """256 LTI instances, nx 48, nu 16, N 1000 (bounds active on about a fifth of the inputs).
+    (1) A fixed number of iterations (plain and accelerated) of the tensor-core schedule
+    (family 6, FP32), of the blocked lane groups (family 5, FP32) and of the plain lane groups
+    in FP64 (family 0): time per iteration, iterate traffic against the measured HBM peak.
+    (2) Solved to c <= 1e-5 (accelerated, at most 20000 iterations) in FP32 on the tensor cores:
+    seconds per solve and iterations; the FP64 time to the same tolerance is its iterations
+    times its measured time per accelerated iteration (running it takes minutes). Device-memory
+    solves timed with CUDA events."""
     insts = W.large_lti()
-    res = {}
-    outs = {}
-    for name, prec, word in (("f32", pimpc.F32, 4), ("f64", pimpc.F64, 8)):
-        s = pimpc.Solver(insts, precision=prec, eps=-1.0, max_iters=iters, accel=1)
-        s.solve()
+    peak, _ = load_peaks()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    p = pimpc.pack(insts)
+    x0 = torch.from_numpy(p["x0"]).to(dev)
+    ref = torch.from_numpy(p["ref"]).to(dev)
+    tu = int(np.sum(p["N"] * p["nu"]))
+    tx = int(np.sum(p["N"] * p["nx"]))
+    n = 64
+
+    def timed(s, reps=2):
+        u = torch.zeros(tu, dtype=torch.float64, device=dev)
+        x = torch.zeros(tx, dtype=torch.float64, device=dev)
+        pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+        b.record(stream)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = s.solve()
-        dt = time.perf_counter() - t0
         its = np.zeros(len(insts), np.int32)
         mom = np.zeros(len(insts), np.int32)
         pimpc.pimpc_get_stats(s.h, its, None, None, mom)
-        n = 64
-        alg = float(np.sum(1000 * (its.astype(np.int64) * 10 * n + mom * 5 * n))) * word
-        res[name] = dict(seconds_per_solve=dt, iterations=iters, ms_per_iteration=1e3 * dt / iters,
-                         stage_iters_per_s=float(np.sum(its) * 1000 / dt),
-                         iterate_gb_per_s=alg / dt / 1e9)
-        outs[name] = r
-        s.close()
-    diff = max(float(np.max(np.abs(np.concatenate([a.ravel(), b.ravel()]) -
-                                   np.concatenate([c.ravel(), e.ravel()])))
-                     / max(1.0, np.max(np.abs(np.concatenate([c.ravel(), e.ravel()])))))
-               for a, b, c, e in zip(outs["f32"]["u"], outs["f32"]["x"], outs["f64"]["u"],
-                                     outs["f64"]["x"]))
-    res.update(max_rel_diff_f32_vs_f64=diff, instances=len(insts), N=1000, nx=48, nu=16,
-               note="wall time of a host-memory solve; iterates only: stage matrices are shared")
+        return a.elapsed_time(b) / reps, its, mom, u.cpu().numpy(), x.cpu().numpy()
+
+    res = dict(instances=len(insts), N=1000, nx=48, nu=16, fixed_iterations=iters)
+    for name, prec, fam, word in (("f32_tensor_cores", pimpc.F32, 6, 4),
+                                  ("f32_blocked_lanes", pimpc.F32, 5, 4),
+                                  ("f64_lanes", pimpc.F64, 0, 8)):
+        row = {}
+        its_fixed = iters if prec == pimpc.F32 else iters // 4
+        for accel in (0, 1):
+            s = pimpc.Solver(insts, precision=prec, eps=-1.0, max_iters=its_fixed, accel=accel)
+            s.set_schedule(fam)
+            ms, its, mom, _, _ = timed(s, reps=2 if prec == pimpc.F32 else 1)
+            alg = float(np.sum(1000 * (its.astype(np.int64) * 10 * n + mom * 5 * n))) * word
+            row["plain" if accel == 0 else "accel"] = dict(
+                ms_per_iteration=ms / its_fixed, iterate_gb_per_s=alg / (ms / 1e3) / 1e9,
+                frac_of_measured_hbm=alg / (ms / 1e3) / 1e9 / peak)
+            s.close()
+        res[name] = row
+    s = pimpc.Solver(insts, precision=pimpc.F32, eps=1e-5, max_iters=20000, accel=1)
+    s.set_schedule(6)
+    ms, its, _, _, _ = timed(s, reps=1)
+    st = np.zeros(len(insts), np.int32)
+    pimpc.pimpc_get_stats(s.h, None, None, st, None)
+    s.close()
+    res["f32_tensor_cores_to_1e-5"] = dict(
+        seconds_per_solve=ms / 1e3, mean_iterations=float(np.mean(its)),
+        converged=int(np.sum(st == pimpc.CONVERGED)), max_iterations=20000)
+    res["f64_lanes_to_1e-5_estimate_s"] = float(
+        np.sum(its) / len(insts) * res["f64_lanes"]["accel"]["ms_per_iteration"] / 1e3)
+    res["note"] = ("iterate traffic: per stage-iteration 10 n words (read, write) plus 5 n on "
+                   "momentum iterations; the stage matrices are shared by all stages")
     return res
+
+
+def profile_large_lti(args, torch, pimpc, W):
+    """Profiling driver on the large-state LTI workload (nx 48, nu 16, N 1000; --batch
+    instances, default 256): FP32, plain iterations, --fixed-iters of them, the schedule of
+    --family; warm-up + steps solves from device memory. Prints the algorithmic bytes of one
+    solve (iterates only: the stage matrices are shared by every stage)."""
+    insts = W.large_lti(batch=args.batch or 256)
+    iters = args.fixed_iters or 10
+    s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=iters, accel=0)
+    if args.family >= 0:
+        s.set_schedule(args.family)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x0 = torch.from_numpy(s.p["x0"]).to(dev)
+    ref = torch.from_numpy(s.p["ref"]).to(dev)
+    u = torch.zeros(int(np.sum(s.N * s.nu)), dtype=torch.float64, device=dev)
+    x = torch.zeros(int(np.sum(s.N * s.nx)), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup + args.steps):
+        pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+    torch.cuda.synchronize()
+    n = 64
+    alg = float(len(insts) * 1000 * iters * 10 * n * 4)
+    print(json.dumps(dict(profile=True, workload="large_lti", instances=len(insts),
+                          family=s.schedule()["family"], iterations=iters,
+                          algorithmic_bytes_per_solve=alg)), flush=True)
+    s.close()
+    return 0
 
 
 def run_reference(args):
@@ -619,10 +684,14 @@ def run_ours(args):
                                   cfg["stall_rel"])
         return h
 
+    if args.profile and args.profile_workload == "large_lti":
+        return profile_large_lti(args, torch, pimpc, W)
     if args.profile:
         eps = -1.0 if args.fixed_iters else cfg["eps"]
         iters_cap = args.fixed_iters or cfg["max_iters"]
         h = make(pimpc.F32, eps, iters_cap)
+        if args.family >= 0:
+            pimpc.pimpc_set_schedule(h, args.family, 0, 0)
         u = torch.zeros(tot_u, dtype=torch.float64, device=dev)
         x = torch.zeros(tot_x, dtype=torch.float64, device=dev)
         for _ in range(args.warmup + args.steps):
