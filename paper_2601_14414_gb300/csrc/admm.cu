@@ -101,7 +101,8 @@ __device__ inline T clampv(T x, T lo, T hi) {
 // ---------------------------------------------------------------------------------------------
 // The persistent kernel.
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+// kSets: compiled with the projection onto non-box input sets (see the blocked kernel).
+template <typename T, bool kSets>
 __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -156,9 +157,9 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
       const T *ref = a.ref ? (a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j])) : nullptr;
       const int refstride = a.ref_per_stage ? n : 0;
       const T *lo = a.lo + a.L.off_n[j], *hi = a.hi + a.L.off_n[j];
-      const int ukind = a.uset_kind ? a.uset_kind[j] : uset::kUsetBox;  // input set U
-      const T ur = a.uset_kind ? a.uset_r[j] : (T)0;
-      const T *ua = a.uset_a ? a.uset_a + a.L.off_n[j] : nullptr;
+      const int ukind = kSets && a.uset_kind ? a.uset_kind[j] : uset::kUsetBox;  // input set U
+      const T ur = kSets && a.uset_kind ? a.uset_r[j] : (T)0;
+      const T *ua = kSets && a.uset_a ? a.uset_a + a.L.off_n[j] : nullptr;
       const int grp = tid / g, l = tid - grp * g;
       const unsigned gmask = g == 32 ? 0xffffffffu : (((1u << g) - 1u) << ((tid & 31) & ~(g - 1)));
       const int ncl = (g == 32 && n > 32) ? 2 : 1;
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
             }
           }
           // Input part onto a non-box set U (warp-wide; the kind is the same for the CTA's item).
-          if (ukind != uset::kUsetBox)
+          if (kSets && ukind != uset::kUsetBox)
             uset::project_inputs<T, 2>(ukind, ur, av, wv, cv, nx, n, g,
                                        [](int jj) { return jj & 31; }, [](int jj) { return jj >> 5; });
           for (int qq = 0; qq < ncl && active; ++qq) {
@@ -425,7 +426,7 @@ cudaError_t launch_t(const AdmmLaunch &s, cudaStream_t stream) {
   Smem lay = layout_of<T>(s);
   a.capI = lay.capI;
   void *params[] = {&a, &lay};
-  return ls::launch_sequence<T>(s, a, (const void *)admm_kernel<T>, params,
+  return ls::launch_sequence<T>(s, a, s.uset_kind ? (const void *)admm_kernel<T, true> : (const void *)admm_kernel<T, false>, params,
                                 (size_t)lay.total * sizeof(T), stream);
 }
 
@@ -444,13 +445,13 @@ cudaError_t admm_configure(int precision, size_t smem, int *blocks_per_sm) {
   cudaError_t rc;
   const int threads = admm_threads(precision);
   if (precision == 0) {
-    rc = cudaFuncSetAttribute(admm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rc = cudaFuncSetAttribute(admm_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (rc != cudaSuccess) return rc;
-    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, admm_kernel<float>, threads, smem);
+    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, admm_kernel<float, false>, threads, smem);
   } else {
-    rc = cudaFuncSetAttribute(admm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rc = cudaFuncSetAttribute(admm_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (rc != cudaSuccess) return rc;
-    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, admm_kernel<double>, threads, smem);
+    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, admm_kernel<double, false>, threads, smem);
   }
   return rc;
 }

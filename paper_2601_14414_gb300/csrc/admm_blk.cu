@@ -149,7 +149,9 @@ __device__ __forceinline__ V4<T> hat4(const T *cur, const T *prev, bool use_prev
   return x;
 }
 
-template <typename T>
+// kSets: compiled with the projection onto non-box input sets; the batches without them run the
+// variant that has only the box.
+template <typename T, bool kSets>
 __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
@@ -205,9 +207,9 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       const T *ref = a.ref ? (a.ref + (a.ref_per_stage ? a.L.Nn[j] : a.L.off_n[j])) : nullptr;
       const int refstride = a.ref_per_stage ? n : 0;
       const T *lo = a.lo + a.L.off_n[j], *hi = a.hi + a.L.off_n[j];
-      const int ukind = a.uset_kind ? a.uset_kind[j] : uset::kUsetBox;  // input set U
-      const T ur = a.uset_kind ? a.uset_r[j] : (T)0;
-      const T *ua = a.uset_a ? a.uset_a + a.L.off_n[j] : nullptr;
+      const int ukind = kSets && a.uset_kind ? a.uset_kind[j] : uset::kUsetBox;  // input set U
+      const T ur = kSets && a.uset_kind ? a.uset_r[j] : (T)0;
+      const T *ua = kSets && a.uset_a ? a.uset_a + a.L.off_n[j] : nullptr;
       const int grp = tid / g, l = tid - grp * g;
       const int c0 = 4 * l;
       const bool own = c0 < n;
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
               }
             }
           }
-          if (ukind != uset::kUsetBox)
+          if (kSets && ukind != uset::kUsetBox)
             uset::project_inputs<T, 4>(ukind, ur, av, wv, cv, nx, n, g,
                                        [](int jj) { return jj >> 2; }, [](int jj) { return jj & 3; });
           if (mine) {
@@ -534,13 +536,13 @@ int64_t blk_region_words(int nx, int nu, int lti, int precision, int S) {
 cudaError_t blk_configure(int precision, size_t smem, int *blocks_per_sm) {
   cudaError_t rc;
   if (precision == 0) {
-    rc = cudaFuncSetAttribute(blk_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rc = cudaFuncSetAttribute(blk_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (rc != cudaSuccess) return rc;
-    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, blk_kernel<float>, kThreads, smem);
+    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, blk_kernel<float, false>, kThreads, smem);
   } else {
-    rc = cudaFuncSetAttribute(blk_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rc = cudaFuncSetAttribute(blk_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (rc != cudaSuccess) return rc;
-    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, blk_kernel<double>, kThreads, smem);
+    rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, blk_kernel<double, false>, kThreads, smem);
   }
   return rc;
 }
@@ -549,11 +551,13 @@ cudaError_t launch_blk(const AdmmLaunch &s, int precision, size_t smem, cudaStre
   if (precision == 0) {
     ls::Args<float> a = ls::make_args<float>(s);
     void *params[] = {&a};
-    return ls::launch_sequence<float>(s, a, (const void *)blk_kernel<float>, params, smem, stream);
+    const void *k = s.uset_kind ? (const void *)blk_kernel<float, true> : (const void *)blk_kernel<float, false>;
+    return ls::launch_sequence<float>(s, a, k, params, smem, stream);
   }
   ls::Args<double> a = ls::make_args<double>(s);
   void *params[] = {&a};
-  return ls::launch_sequence<double>(s, a, (const void *)blk_kernel<double>, params, smem, stream);
+  const void *k = s.uset_kind ? (const void *)blk_kernel<double, true> : (const void *)blk_kernel<double, false>;
+  return ls::launch_sequence<double>(s, a, k, params, smem, stream);
 }
 
 }  // namespace pimpc
