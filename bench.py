@@ -314,12 +314,28 @@ def bench_polish(torch, pimpc, make, d, p, cfg, tot_u, tot_x, refs, ou, ox):
                 steps=1, warmup=1)
 
 
-def bench_cartpole(torch, pimpc, W, steps):
+def fp32_peak_tflops():
+    """FP32 CUDA-core peak of the part from its unit counts and clock: 152 SMs x 128 FP32 lanes x
+    2 flops per fused multiply-add x the SM clock (the measured maximum in MEASURED_PEAKS.json,
+    else 2070 MHz)."""
+    mhz = 2070.0
+    path = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def bench_cartpole(torch, pimpc, W, steps, family=None):
     """Differentiable MPC: 1024 cart-pole instances (N = 100), 150 plain FP32 iterations,
-    forward solve + reverse sweep with checkpoints every 25 iterations, device memory."""
+    forward solve + reverse sweep with checkpoints every 25 iterations, device memory.
+    ``family``: the forward solve's schedule (None: the default). The roofline is the FP32 ALU
+    one: forward flops per stage-iteration 2 n^2 + 4 nx n + 4 nx nu + 2 nu^2 + 40 n (the
+    products and the elementwise steps, n = nx + nu)."""
     insts = W.cartpole_batch()
     iters, K = 150, 25
     s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=iters, accel=0)
+    if family is not None:
+        s.set_schedule(family)
     prm = np.ascontiguousarray(np.concatenate([i["params"] for i in insts]))
     xb = np.ascontiguousarray(np.concatenate([i["op_x"] for i in insts]))
     ub = np.ascontiguousarray(np.concatenate([i["op_u"] for i in insts]))
@@ -358,10 +374,52 @@ def bench_cartpole(torch, pimpc, W, steps):
     torch.cuda.synchronize()
     f_ms = float(np.mean([ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(steps)]))
     b_ms = float(np.mean([ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(steps)]))
+    fam = s.schedule()["family"]
     s.close()
+    nx, nu, n = 4, 1, 5
+    flops = float(len(insts) * 100 * iters * (2 * n * n + 4 * nx * n + 4 * nx * nu + 2 * nu * nu + 40 * n))
+    peak = fp32_peak_tflops()
+    fwd_tf = flops / (f_ms / 1e3) / 1e12
     return dict(value=len(insts) / ((f_ms + b_ms) / 1e3), unit="forward+backward solves/s",
                 forward_ms=f_ms, backward_ms=b_ms, instances=len(insts), N=100, iterations=iters,
-                checkpoint_every=K, dtype="f32", steps=steps, warmup=2)
+                checkpoint_every=K, dtype="f32", steps=steps, warmup=2, forward_family=fam,
+                roofline=dict(bound="alu", achieved=fwd_tf, peak=peak, unit="TFLOP/s",
+                              frac=fwd_tf / peak, forward_flops=flops,
+                              peak_kind="derived: 152 SMs x 128 FP32 lanes x 2 x SM clock",
+                              note="forward solve; the backward sweep is about three forward "
+                                   "passes per iteration (recompute and reverse)"),
+                forward_plus_backward_frac=(4 * flops / ((f_ms + b_ms) / 1e3) / 1e12) / peak)
+
+
+def bench_temporal_blocking(torch, pimpc, W, cfg, iters=64):
+    """Plain iterations (accel = 0, fixed count) on the batched workload: the blocked lane groups
+    (family 5, one pass over the stage data per iteration) against temporal blocking (family 7,
+    one pass per T iterations), and the one-pass roofline bound (algorithmic bytes of one plain
+    iteration over the measured HBM peak)."""
+    insts = W.batched_uneven(seed=cfg["seed"], batch=cfg["batch"])
+    p = pimpc.pack(insts)
+    nx, nu, N = p["nx"].astype(np.int64), p["nu"].astype(np.int64), p["N"].astype(np.int64)
+    peak, _ = load_peaks()
+    one = algorithmic_bytes(nx, nu, N, np.ones(len(insts), np.int64), np.zeros(len(insts), np.int64), 4)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    x0, ref = torch.from_numpy(p["x0"]).to(dev), torch.from_numpy(p["ref"]).to(dev)
+    res = dict(iterations=iters, one_pass_bound_ms_per_iteration=one / peak / 1e6,
+               one_pass_bytes_per_iteration=one)
+    for name, fam, T in (("blocked_lanes", 5, 0), ("temporal_T4", 7, 4), ("temporal_T8", 7, 8)):
+        s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=iters, accel=0)
+        s.set_schedule(fam, 0, T)
+        u = torch.zeros(int(np.sum(N * nu)), dtype=torch.float64, device=dev)
+        x = torch.zeros(int(np.sum(N * nx)), dtype=torch.float64, device=dev)
+        pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pimpc.pimpc_solve(s.h, x0, None, ref, False, 0, u, x)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name + "_ms_per_iteration"] = a.elapsed_time(b) / iters
+        s.close()
+    return res
 
 
 def bench_latency(torch, pimpc, W, reps=50):
@@ -872,7 +930,10 @@ def run_ours(args):
             fp64_polish=extra(bench_polish, torch, pimpc, make, d, p, cfg, tot_u, tot_x, (ur, xr),
                               ou, ox),
             differentiable_cartpole=extra(bench_cartpole, torch, pimpc, W, args.steps),
+            differentiable_cartpole_resident=extra(bench_cartpole, torch, pimpc, W, args.steps,
+                                                   family=pimpc.FAMILY_RESIDENT),
             single_instance_latency=extra(bench_latency, torch, pimpc, W),
+            temporal_blocking_plain=extra(bench_temporal_blocking, torch, pimpc, W, cfg),
             quadrotor_rti_f64=extra(bench_rti, torch, pimpc, W, pimpc.F64),
             quadrotor_rti_f32=extra(bench_rti, torch, pimpc, W, pimpc.F32),
             quadrotor_rti_f64_resident=extra(bench_rti, torch, pimpc, W, pimpc.F64,

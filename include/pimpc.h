@@ -328,9 +328,12 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
  *                   FP32 iterations); 6: stage-invariant instances with FP32 iterations, the
  *                   per-stage products of 127-stage tiles as matrix products on the tensor
  *                   cores (tcgen05, TF32 operands split in two for FP32 accuracy; nx and nu
- *                   rounded up to 16 must sum to 64 or less, nu's at most nx's); -1: the
- *                   default.
- *   ctas_per_sm  families 2, 4 and 5: CTAs per SM the shared-memory budget of a CTA is sized
+ *                   rounded up to 16 must sum to 64 or less, nu's at most nx's); 7: temporal
+ *                   blocking of the plain iteration (accel = 0 only): windows of stages loaded
+ *                   once into shared memory, iterated T times there with T halo stages on each
+ *                   open side and written back on their interior, the stop test every T
+ *                   iterations; -1: the default.
+ *   ctas_per_sm  families 2, 4, 5 and 7: CTAs per SM the shared-memory budget of a CTA is sized
  *                for (0 = 2 for family 2, 1 for family 4; for family 5 the one of 3, 2, 1 that
  *                fits every instance with the most stages in flight); ignored by families 0
  *                and 3.
@@ -341,7 +344,8 @@ int pimpc_backward(pimpc_solver *s, const double *dL_du, const double *dL_dx, do
  *                8 or 16 (0 = the fewest whose shared memory holds the instance, or the most
  *                that leave each CTA four stages when the batch occupies few SMs); family 4:
  *                stages per block (0 = as many as the shared memory holds, at most 128);
- *                family 6: 127-stage tiles per work item (0 = 2).
+ *                family 6: 127-stage tiles per work item (0 = 2); family 7: T, iterations per
+ *                block (0 = 8).
  * pimpc_set_schedule re-lays out the stage data and the iterates: the next solve factorises
  * again and starts cold (warm_start is treated as 0 until one solve has run).
  * Errors: PIMPC_EINVAL (a bad value, or an instance that does not fit the schedule; the

@@ -138,8 +138,8 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   // families are chosen explicitly or by the autotuner.
   if (sc.family < 0) sc.family = precision == PIMPC_F32 ? 5 : 0;
   if (sc.family != 0 && sc.family != 2 && sc.family != 3 && sc.family != 4 && sc.family != 5 &&
-      sc.family != 6) {
-    why = "schedule family must be 0, 2, 3, 4, 5 or 6";
+      sc.family != 6 && sc.family != 7) {
+    why = "schedule family must be 0, 2, 3, 4, 5, 6 or 7";
     return PIMPC_EINVAL;
   }
   if (sc.family == 6) {
@@ -201,7 +201,56 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   cudaError_t e = cudaSuccess;
   std::vector<int64_t> tc_off(batch, 0);
   int64_t tot_tc = 0;
-  if (sc.family == 6) {
+  if (sc.family == 7) {
+    // Windows: per instance the widest window (interior plus T stages on each side) whose shared
+    // memory fits the budget of cps CTAs per SM; an instance that fits whole is one closed window.
+    const int T = sc.item_scale > 0 ? sc.item_scale : 8;
+    const int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 1;
+    const int64_t budget =
+        std::min<int64_t>((int64_t)smem_sm / cps - 1024 - 256, optin - 256) / 128 * 128;
+    std::vector<int> S(batch), inner(batch);
+    for (int j = 0; j < batch; ++j) {
+      const int n = nx[j] + nu[j];
+      W[j] = block_words(nx[j], nu[j]);
+      blk[j] = tot_blk;
+      tot_blk += ((int64_t)blocks_per_instance(lti, N[j]) * W[j] + 31) / 32 * 32;
+      Ni[j] = tot_Ni;
+      tot_Ni += ((int64_t)N[j] * admm_iter_stride(n, precision) + 31) / 32 * 32;
+      int lo = 1, hi = N[j];  // the widest window that fits, up to the whole horizon
+      if (tb_window_words(nx[j], nu[j], W[j], lti, precision, 1) * (int64_t)ts > budget) lo = 0;
+      while (lo > 0 && lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (tb_window_words(nx[j], nu[j], W[j], lti, precision, mid) * (int64_t)ts <= budget) lo = mid;
+        else hi = mid - 1;
+      }
+      S[j] = lo;
+      inner[j] = S[j] >= N[j] ? N[j] : S[j] - 2 * T;
+      if (inner[j] < 1) {
+        char b[200];
+        snprintf(b, sizeof b, "instance %d: a window of %d stages leaves no interior at T = %d", j,
+                 S[j], T);
+        why = b;
+        return PIMPC_EINVAL;
+      }
+      S[j] = std::min(N[j], inner[j] + 2 * T);
+    }
+    for (int oi = 0; oi < batch; ++oi) {
+      const int j = order[oi];
+      for (int a0 = 0; a0 < N[j]; a0 += inner[j]) {
+        item_inst.push_back(j);
+        item_a.push_back(a0);
+        item_b.push_back(std::min(N[j], a0 + inner[j]));
+        nitems_inst[j] += 1;
+      }
+    }
+    size_t smem = 0;
+    for (int j = 0; j < batch; ++j)
+      smem = std::max(smem, (size_t)tb_window_words(nx[j], nu[j], W[j], lti, precision, S[j]) * ts);
+    s->tb_T = T;
+    P.threads = tb_threads();
+    s->smem_admm = smem;
+    e = tb_configure(precision, smem, &bps);
+  } else if (sc.family == 6) {
     // Tiles of 127 stages (128 MMA rows with the stage before the tile); items of a few tiles
     // so that an instance's matrices are copied to shared memory once per item.
     const int tpi = sc.item_scale > 0 ? sc.item_scale : 2;
@@ -641,11 +690,14 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.coef_tab = s->coef_tab;
   if (s->sched.family == 3 && s->coef_len < s->max_iters + 1)
     return fail(s, PIMPC_ESTATE, "momentum table shorter than max_iters");
+  if (s->sched.family == 7 && s->accel)
+    return fail(s, PIMPC_ESTATE, "temporal blocking (schedule 7) runs the plain iteration: accel must be 0");
   PIMPC_CHECK(s, s->tiled == 2 ? launch_tile(a, st)
                  : s->tiled == 3 ? launch_blk(a, s->prec, s->smem_admm, st)
                  : s->sched.family == 3 ? launch_resident(a, s->prec, s->res_plan, s->smem_admm, st)
                  : s->sched.family == 4 ? launch_gemm(a, s->prec, s->gemm_plan, st)
                  : s->sched.family == 6 ? launch_tc(a, s->tc_mat, s->tc_off, s->smem_admm, st)
+                 : s->sched.family == 7 ? launch_tb(a, s->prec, s->tb_T, s->smem_admm, st)
                                         : launch_admm(a, s->prec, st),
               "solve");
   s->solved = true;

@@ -99,6 +99,12 @@ cudaError_t tc_configure(size_t smem, int *blocks_per_sm);
 cudaError_t launch_tc(const AdmmLaunch &s, const float *tcm, const int64_t *tc_off, size_t smem,
                       cudaStream_t stream);
 
+// Temporal blocking of the plain iteration: windows of stages iterated T times in shared memory.
+int tb_threads();
+int64_t tb_window_words(int nx, int nu, int W, int lti, int precision, int S);
+cudaError_t tb_configure(int precision, size_t smem, int *blocks_per_sm);
+cudaError_t launch_tb(const AdmmLaunch &s, int precision, int T, size_t smem, cudaStream_t stream);
+
 // Schedule of the batched solve: which kernel family and how its work is cut.
 struct Schedule {
   int family = -1;       // 0: lane groups on plain stage blocks; 2: one thread per stage on halo
@@ -107,8 +113,8 @@ struct Schedule {
                          // instance, 0: the fewest that fit); 4: stage-invariant instances as
                          // dense contractions over blocks of stages; 5: lane groups owning
                          // 4-column blocks on blocked stage blocks; 6: stage-invariant FP32
-                         // instances with the stage products on the tensor cores; -1: the
-                         // default
+                         // instances with the stage products on the tensor cores; 7: temporal
+                         // blocking of the plain iteration (item_scale = T); -1: the default
   int ctas_per_sm = 0;   // halo tiles and blocked lane groups: CTAs per SM the shared-memory
                          // budget is sized for (0: 2 for halo tiles, 3 for blocked lane groups)
   int item_scale = 0;    // lane groups: sub-chunks per item (0: automatic);

@@ -44,6 +44,7 @@ struct pimpc_solver {
   int *itfirst = nullptr;
   float *tc_mat = nullptr;       // tensor-core schedule: per-instance matrix blocks
   int64_t *tc_off = nullptr;     // [batch] word offsets of those blocks
+  int tb_T = 8;  // temporal blocking: iterations per block
   double *cbest = nullptr;
   int *itbest = nullptr;
   // input sets (pimpc_set_input_set): device kind [batch], r [batch] and normal [sum n] in the

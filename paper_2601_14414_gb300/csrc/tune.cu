@@ -79,6 +79,11 @@ int pimpc_autotune(pimpc_solver *s, int trial_iters, int *family, int *ctas_per_
     c.family = 4;  // stage-invariant instances as dense contractions
     cands.push_back(c);
   }
+  if (!s->accel) {
+    Schedule c;
+    c.family = 7;  // temporal blocking of the plain iteration
+    cands.push_back(c);
+  }
   if (s->lti && s->prec == PIMPC_F32) {
     Schedule c;
     c.family = 6;  // stage products on the tensor cores: skipped below when the sizes do not fit
