@@ -24,7 +24,7 @@ BATCHED_UNEVEN = dict(
     accuracy=1e-4,     # a solve counts when max|w - w*| / max(1, max|w*|) <= accuracy
     ref_eps=1e-20,     # FP64 reference solve (same GPU) used to score accuracy
     ref_max_iters=20000,
-    oracle_score_sample=32,  # instances also scored against the converged FP64 oracle
+    oracle_score_sample=64,  # instances also scored against the converged FP64 oracle
     polish_iters=2000,  # FP64 polish variant: FP64 iterations after the FP32 ones ...
     polish_eps=1e-13,   # ... until c <= polish_eps
 )
