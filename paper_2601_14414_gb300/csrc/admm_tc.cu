@@ -17,9 +17,9 @@
 //
 // A tile is 128 rows: row 0 is the stage before the tile (its xbar_{k+1} = H h feeds the tile's
 // first stage, so it is recomputed here instead of read from a neighbour), rows 1 .. 127 are the
-// tile's 127 stages. One CTA (256 threads) per SM; thread t owns row 32 (w % 4) + lane of its
-// warp w, which is the tensor-memory lane its warp may read, and the warps w and w + 4 split the
-// row's components in 16-column chunks. The instance's matrices (hi and lo halves, in the
+// tile's 127 stages. One CTA (512 threads) per SM; thread t owns row 32 (w % 4) + lane of its
+// warp w, which is the tensor-memory lane its warp may read, and the warps w, w + 4, w + 8 and
+// w + 12 split the row's components in 16-column chunks. The instance's matrices (hi and lo halves, in the
 // canonical K-major core-matrix layout) come to shared memory with one bulk copy per work item
 // from a per-instance block that a prepare kernel builds from the FP32 stage cache. Iterates are
 // stored in tiles of 128 stages, component-major inside a tile, so that the threads of a warp
@@ -42,7 +42,8 @@ using ls::Args;
 
 constexpr int kRows = 128;         // MMA M: stages per tile plus the halo row
 constexpr int kTile = kRows - 1;   // stages a tile updates
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kSplit = kThreads / 128;  // warps sharing a TMEM lane quarter split the columns
 constexpr uint32_t kTmemCols = 256;
 
 // Padded sizes (x part and u part each rounded up to 16 columns) and the per-instance matrix
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
   __shared__ double sRed[kThreads / 32];
   float *sm = reinterpret_cast<float *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, half = warp >> 2;
+  const int quarter = warp & 3, half = warp >> 2;  // half: this warp's column share (0 .. kSplit-1)
   const int r = 32 * quarter + lane;  // this thread's MMA row / TMEM lane
   const unsigned nblocks = gridDim.x;
   Ctl *ctl = a.ctl;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
         const bool last = r == kRows - 1 && k + 1 < N;  // the last row also needs stage k + 1
 
         // ---- phase A: W = vhat - betahat (x part) and y (of the next stage, one row up) ----
-        for (int qc = half; qc < nch; qc += 2) {
+        for (int qc = half; qc < nch; qc += kSplit) {
           const bool xq = qc < nchx;
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
 
         // ---- phase B: t + W_u (input of G2), then h (input of G4, in bufA once G2 is done) ----
         wait_g(0);
-        for (int qc = nchx + half; qc < nch; qc += 2) {
+        for (int qc = nchx + half; qc < nch; qc += kSplit) {
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
             const int p0 = 16 * qc + 4 * q4;
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
         }
         wait_g(1);
         wait_g(2);  // G2 has read bufA: h may overwrite it
-        for (int qc = half; qc < nch; qc += 2) {
+        for (int qc = half; qc < nch; qc += kSplit) {
           const bool xq = qc < nchx;
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
 
         // ---- phase C: du (input of G6, bufB columns 0 .. nup), then xbar shifted one row down
         // (input of G5, in bufA once G4 is done) ----
-        for (int qc = nchx + half; qc < nch; qc += 2) {
+        for (int qc = nchx + half; qc < nch; qc += kSplit) {
           const int su = qc - nchx;  // u chunk: du columns 16 su .. 16 su + 15
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
           commit(4);
         }
         wait_g(3);
-        for (int qc = half; qc < nch; qc += 2) {
+        for (int qc = half; qc < nch; qc += kSplit) {
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
             const int p0 = 16 * qc + 4 * q4;
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
         // ---- phase D: steps 2-4 on the tile's stages ----
         wait_g(4);
         wait_g(5);
-        for (int qc = half; qc < nch; qc += 2) {
+        for (int qc = half; qc < nch; qc += kSplit) {
           const bool xq = qc < nchx;
 #pragma unroll 2
           for (int q4 = 0; q4 < 4; ++q4) {
