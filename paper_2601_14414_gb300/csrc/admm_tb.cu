@@ -30,6 +30,8 @@ namespace {
 template <typename T>
 using Args = ls::Args<T>;
 
+constexpr int kTbThreads = 512;
+
 struct TbPlan {
   int T;  // iterations per block
 };
@@ -51,7 +53,7 @@ __host__ __device__ inline TbRegions tb_regions(int n, int W, int lti, int ts, i
   R.offX = R.offI + 2 * R.itb;
   R.offD = R.offX + up((L + 1) * nv);
   R.offS = R.offD + up(L * nv);
-  R.total = R.offS + up((256 / tb_group(n)) * 4 * nv);
+  R.total = R.offS + up((kTbThreads / tb_group(n)) * 4 * nv);
   return R;
 }
 
@@ -89,9 +91,9 @@ __device__ inline void finish_block(const Args<T> &a, int j, int blk, int iters,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) tb_kernel(Args<T> a, TbPlan pl) {
+__global__ void __launch_bounds__(kTbThreads) tb_kernel(Args<T> a, TbPlan pl) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ double sRed[8];
+  __shared__ double sRed[kTbThreads / 32];
   __shared__ int sItem, sOk;
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x, nthreads = blockDim.x;
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(256) tb_kernel(Args<T> a, TbPlan pl) {
 
 }  // namespace
 
-int tb_threads() { return 256; }
+int tb_threads() { return kTbThreads; }
 
 // Shared-memory words of a window of S stages (one instance).
 int64_t tb_window_words(int nx, int nu, int W, int lti, int precision, int S) {
@@ -295,11 +297,11 @@ cudaError_t tb_configure(int precision, size_t smem, int *blocks_per_sm) {
   if (precision == 0) {
     rc = cudaFuncSetAttribute(tb_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (rc != cudaSuccess) return rc;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tb_kernel<float>, 256, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tb_kernel<float>, kTbThreads, smem);
   }
   rc = cudaFuncSetAttribute(tb_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (rc != cudaSuccess) return rc;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tb_kernel<double>, 256, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tb_kernel<double>, kTbThreads, smem);
 }
 
 cudaError_t launch_tb(const AdmmLaunch &s, int precision, int T, size_t smem, cudaStream_t stream) {
