@@ -44,7 +44,7 @@ constexpr int kRows = 128;         // MMA M: stages per tile plus the halo row
 constexpr int kTile = kRows - 1;   // stages a tile updates
 constexpr int kThreads = 512;
 constexpr int kSplit = kThreads / 128;  // warps sharing a TMEM lane quarter split the columns
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 512;  // 256 accumulator columns, 256 for the row's hats
 
 // Padded sizes (x part and u part each rounded up to 16 columns) and the per-instance matrix
 // block: each operand as its TF32 hi half followed by its lo half (rows x K, core-matrix layout).
@@ -311,6 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
       };
       const uint32_t cT = 0, cDU = (uint32_t)nup, cQ = 2u * nup, cXB = cQ + (uint32_t)np;
       const uint32_t cAX = cXB + (uint32_t)np, cBD = cAX + (uint32_t)nxp;
+      // The row's hats zhat, vhat, betahat, lambdahat (loaded in phase A) kept in tensor memory
+      // columns 256 + b np + p for phases B and D (thetahat is read where it is used).
+      auto cHat = [&](int b) -> uint32_t { return 256u + (uint32_t)(b * np); };
       const int nch = np / 16, nchx = nxp / 16;
       // padded columns that hold no component (x part beyond nx, u part beyond nu) stay zero
       auto valid4 = [&](int p0, int i) -> bool {
@@ -347,17 +350,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
           for (int q4 = 0; q4 < 4; ++q4) {
             const int p0 = 16 * qc + 4 * q4;
             float4 y4 = make_float4(0.f, 0.f, 0.f, 0.f), w4 = y4, yn4 = y4;
+            float4 z4 = y4, v4 = y4, l4 = y4, b4 = y4;
             if (inb) {
-              const float4 z4 = hat4(0, k, p0), v4 = hat4(1, k, p0), l4 = hat4(4, k, p0);
+              z4 = hat4(0, k, p0); v4 = hat4(1, k, p0); l4 = hat4(4, k, p0); b4 = hat4(3, k, p0);
               y4 = make_float4(z4.x - v4.x + l4.x, z4.y - v4.y + l4.y, z4.z - v4.z + l4.z,
                                z4.w - v4.w + l4.w);
               if (xq) {
-                const float4 b4 = hat4(3, k, p0);
                 const float4 e4 = *reinterpret_cast<const float4 *>(E + p0);
                 w4 = make_float4(v4.x - b4.x, v4.y - b4.y, v4.z - b4.z, v4.w - b4.w);
                 y4.x -= e4.x; y4.y -= e4.y; y4.z -= e4.z; y4.w -= e4.w;
               }
             }
+            tc::tmem_st4(trow + cHat(0) + p0, z4);
+            tc::tmem_st4(trow + cHat(1) + p0, v4);
+            tc::tmem_st4(trow + cHat(2) + p0, b4);
+            tc::tmem_st4(trow + cHat(3) + p0, l4);
             if (last) {
               const float4 z4 = hat4(0, k + 1, p0), v4 = hat4(1, k + 1, p0), l4 = hat4(4, k + 1, p0);
               yn4 = make_float4(z4.x - v4.x + l4.x, z4.y - v4.y + l4.y, z4.z - v4.z + l4.z,
@@ -377,6 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
             }
           }
         }
+        tc::tmem_wait_st();
         publish();
         if (tid == 0) {
           gemm(cT, sA, 0, nxp, d.o1, nup);
@@ -392,9 +400,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
           for (int q4 = 0; q4 < 4; ++q4) {
             const int p0 = 16 * qc + 4 * q4;
             const float4 t4 = tc::tmem_ld4(trow + cT + (p0 - nxp));
+            const float4 v4 = tc::tmem_ld4(trow + cHat(1) + p0), b4 = tc::tmem_ld4(trow + cHat(2) + p0);
             float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (inb) {
-              const float4 v4 = hat4(1, k, p0), b4 = hat4(3, k, p0);
               v2 = make_float4(t4.x + v4.x - b4.x, t4.y + v4.y - b4.y, t4.z + v4.z - b4.z,
                                t4.w + v4.w - b4.w);
             }
@@ -414,9 +422,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
           for (int q4 = 0; q4 < 4; ++q4) {
             const int p0 = 16 * qc + 4 * q4;
             const float4 q4v = tc::tmem_ld4(trow + cQ + p0);
+            const float4 z4 = tc::tmem_ld4(trow + cHat(0) + p0);
             float4 h4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (inb) {
-              const float4 z4 = hat4(0, k, p0), t4 = hat4(2, k, p0);
+              const float4 t4 = hat4(2, k, p0);
               // y_u of this row (the row below wrote it in phase A)
               const float4 yu4 = xq ? make_float4(0.f, 0.f, 0.f, 0.f)
                                     : *reinterpret_cast<const float4 *>(bufB + tc::core_off(r, p0, np));
@@ -500,9 +509,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
             const float4 ax4 = xq ? tc::tmem_ld4(trow + cAX + p0) : getA4(bufA, r, p0);
             const float4 bd4 = xq ? tc::tmem_ld4(trow + cBD + p0) : tc::tmem_ld4(trow + cDU + (p0 - nxp));
             float4 xn4 = tc::tmem_ld4(trow + cXB + p0);
+            const float4 z4 = tc::tmem_ld4(trow + cHat(0) + p0), v4 = tc::tmem_ld4(trow + cHat(1) + p0);
+            const float4 b4 = tc::tmem_ld4(trow + cHat(2) + p0), l4 = tc::tmem_ld4(trow + cHat(3) + p0);
             if (!own) continue;
-            const float4 z4 = hat4(0, k, p0), v4 = hat4(1, k, p0), t4 = hat4(2, k, p0);
-            const float4 b4 = hat4(3, k, p0), l4 = hat4(4, k, p0);
+            const float4 t4 = hat4(2, k, p0);
             const float4 e4 = xq ? *reinterpret_cast<const float4 *>(E + p0) : make_float4(0.f, 0.f, 0.f, 0.f);
             if (term) {
               const float4 hh = *reinterpret_cast<const float4 *>(sHTh + p0);
