@@ -185,14 +185,24 @@ SOLVE_KERNELS = {
     0: ("admm_kernel<float>", "admm.cu", "admm_kernel_f32_batched_512x30.md"),
     5: ("blk_kernel<float>", "admm_blk.cu", "blk_kernel_f32_batched_512x30.md"),
 }
-# Headers compiled into every solve kernel: a change there changes the kernel too.
-KERNEL_HEADERS = ("lockstep.cuh", "bulk.cuh", "products.cuh", "pimpc_internal.cuh", "launch.h",
-                  "usets.cuh", "tc.cuh")
+def kernel_files(source):
+    """The kernel's source file and the library headers it includes, directly or through another
+    header (a change in any of them changes the compiled kernel)."""
+    csrc = os.path.join(HERE, "paper_2601_14414_gb300", "csrc")
+    seen, todo = set(), [source]
+    while todo:
+        name = todo.pop()
+        path = os.path.join(csrc, name)
+        if name in seen or not os.path.exists(path):
+            continue
+        seen.add(name)
+        todo += re.findall(r'^\s*#include\s+"([^"]+)"', open(path).read(), re.M)
+    return [source] + sorted(seen - {source})
 
 
 def kernel_source_hash(source):
     h = hashlib.sha256()
-    for name in (source,) + KERNEL_HEADERS:
+    for name in kernel_files(source):
         h.update(open(os.path.join(HERE, "paper_2601_14414_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 

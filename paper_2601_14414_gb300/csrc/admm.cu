@@ -8,10 +8,10 @@
 // iteration on their stages; a grid barrier separates iterations. Because Algorithm 1 is
 // parallel in the horizon (every update of stage k reads only stages k-1, k and k+1), an item
 // needs one stage of halo on each side: the block and hats of stage a-1 to recompute
-// xbar_a = H_{a-1} h_{a-1}, and G_b, e_b and the hats of stage b for h_{b-1}. The CTA that
-// finishes the last item of an instance (per-instance atomic counter) owns the reduction of
-// c^{i+1} and applies the stop test (step 5) and the momentum / restart rule (steps 6-7) for that
-// instance. Stopped instances leave the queue (stream compaction after the barrier), so the
+// xbar_a = H_{a-1} h_{a-1}, and G_b, e_b and the hats of stage b for h_{b-1}. Each item stores
+// its share of c^{i+1}; after the barrier one thread per instance sums the shares and applies the
+// stop test (step 5) and the momentum / restart rule (steps 6-7) for that instance. Stopped
+// instances leave the queue (stream compaction after the barrier), so the
 // remaining instances keep every SM busy and an instance that needs many iterations is spread
 // over many CTAs instead of running alone.
 //
@@ -391,18 +391,19 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
       }
       if (!ok) break;
 
-      // ---- step 4: this item's share of c; the last item of the instance applies steps 5-7 ----
+      // ---- step 4: this item's share of c (steps 5-7 follow in the pass after the barrier) ----
       for (int off = 16; off > 0; off >>= 1) cacc += __shfl_xor_sync(0xffffffffu, cacc, off);
       if ((tid & 31) == 0) sRed[tid >> 5] = (double)cacc;
       __syncthreads();
       if (tid == 0) {
         double part = 0.0;
         for (int w = 0; w < (nthreads >> 5); ++w) part += sRed[w];
-        ls::finish_item(a, j, it, part);
+        a.cpart[item] = part;  // steps 5-7 run in the pass after the barrier
       }
     }
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk)) break;
   }

@@ -2,7 +2,7 @@
 // (schedule family 5, tiled layout 3).
 //
 // The frame is the lock-step persistent one of admm.cu (items of consecutive stages pulled from
-// a queue, a grid barrier per iteration, the instance's last item applying steps 5-7, stopped
+// a queue, a grid barrier per iteration, steps 5-7 in the pass over the instances after it, stopped
 // instances compacted away). What differs is how a stage's products map onto lanes.
 //
 // A group of g = 4, 8 or 16 lanes (n <= 16, 32, 64) handles one stage; lane l owns the
@@ -69,29 +69,38 @@ __device__ __forceinline__ void st4(double *p, const V4<double> &x) {
   *reinterpret_cast<double2 *>(p) = make_double2(x.v[0], x.v[1]);
   *reinterpret_cast<double2 *>(p + 2) = make_double2(x.v[2], x.v[3]);
 }
+// Four components of an iterate in global memory, written by other CTAs before the grid
+// barrier (read through L2).
+__device__ __forceinline__ V4<float> ldg4(const float *p) {
+  const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+  return {{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ V4<double> ldg4(const double *p) {
+  const double2 q0 = __ldcg(reinterpret_cast<const double2 *>(p));
+  const double2 q1 = __ldcg(reinterpret_cast<const double2 *>(p + 2));
+  return {{q0.x, q0.y, q1.x, q1.y}};
+}
 template <typename T>
 __device__ __forceinline__ V4<T> zero4() {
   return {{(T)0, (T)0, (T)0, (T)0}};
 }
 
 // Shared-memory regions of a sub-chunk with S groups (elements of T): LTV stage blocks (S - 1
-// blocks and the next stage's G and e), current and previous iterates (S records each), the
-// halo (H_{a-1}, or both blocks of a stage-invariant instance), the halo iterates, per-group
-// scratch (5 vectors), the xbar rows (double-buffered, S rows each) and the instance's Qbar
-// diagonal and bounds.
+// blocks and the next stage's G and e), the halo block (H_{a-1}, or both blocks of a
+// stage-invariant instance), per-group scratch (5 vectors), the xbar rows (double-buffered, S
+// rows each) and the instance's Qbar diagonal and bounds. The iterates do not pass through
+// shared memory: each lane reads its own 16-byte pieces of them from L2, where the previous
+// sub-chunk prefetched them.
 struct Regions {
-  int rawI, capI, haloB, haloI, scr, X, prm, total;
+  int haloB, scr, X, prm, total;
 };
 
 __host__ __device__ inline Regions regions(int nx, int nu, int lti, int tsize, int S) {
-  const int n = nx + nu, nP = bl_pad4(n), rec = bl_rec(n);
+  const int n = nx + nu, nP = bl_pad4(n);
   const int W = bl_block_words(nx, nu, tsize), ge = bl_oH(nx, nu, tsize);
   Regions r;
-  r.rawI = lti ? 0 : bl_pad4((S - 1) * W + ge);
-  r.capI = S * rec;
-  r.haloB = r.rawI + 2 * r.capI;
-  r.haloI = r.haloB + bl_pad4(lti ? 2 * W : bl_sym_words(n));
-  r.scr = r.haloI + 2 * rec;
+  r.haloB = lti ? 0 : bl_pad4((S - 1) * W + ge);
+  r.scr = r.haloB + bl_pad4(lti ? 2 * W : bl_sym_words(n));
   r.X = r.scr + S * 5 * nP;
   r.prm = r.X + 2 * S * nP;  // the instance's Qbar diagonal and bounds (3 vectors)
   r.total = r.prm + 3 * nP;
@@ -137,12 +146,12 @@ __device__ inline T clampv(T x, T lo, T hi) {
   return x < lo ? lo : (x > hi ? hi : x);
 }
 
-// Momentum hat of four components: cur + f (cur - prev).
+// Momentum hat of four components of an iterate in global memory: cur + f (cur - prev).
 template <typename T>
 __device__ __forceinline__ V4<T> hat4(const T *cur, const T *prev, bool use_prev, T f) {
-  V4<T> x = ld4(cur);
+  V4<T> x = ldg4(cur);
   if (use_prev) {
-    const V4<T> p = ld4(prev);
+    const V4<T> p = ldg4(prev);
 #pragma unroll
     for (int i = 0; i < 4; ++i) x.v[i] += f * (x.v[i] - p.v[i]);
   }
@@ -155,7 +164,7 @@ template <typename T, bool kSets>
 __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
-  __shared__ int sItem, sOk;
+  __shared__ int sDesc[4], sOk;
   __shared__ double sRed[kThreads / 32];
   T *sm = reinterpret_cast<T *>(smem_raw);
   constexpr int TS = (int)sizeof(T);
@@ -171,21 +180,37 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
   __syncthreads();
   uint32_t par = 0u;
   bool pend = false;
+  // Thread 0 fetches the next item (queue slot, list entry, item fields: three dependent global
+  // reads) during the current item's last sub-chunk, one step per phase, so that it is known
+  // when the item ends. nstate: 0 nothing fetched, 1 slot taken, 2 item known, 3 ready,
+  // 4 the queue is empty.
+  int nstate = 0, nq = 0, nitem = 0, nj = 0, nka = 0, nkb = 0;
 
   int cl = 0;
   for (int it = 0; it < a.max_iters; ++it) {
     const int nact = *(volatile int *)&ctl->nlist[cl];
     bool ok = true;
+    auto advance = [&]() {  // thread 0: one step of the next item's fetch
+      if (nstate == 1) {
+        if (nq < nact) { nitem = a.list[cl][nq]; nstate = 2; } else { nstate = 4; }
+      } else if (nstate == 2) {
+        nj = a.item_inst[nitem]; nka = a.item_a[nitem]; nkb = a.item_b[nitem]; nstate = 3;
+      }
+    };
     for (;;) {
-      if (tid == 0) sItem = atomicAdd(&ctl->queue[it & 1], 1);
+      if (tid == 0) {
+        if (nstate == 0) { nq = atomicAdd(&ctl->queue[it & 1], 1); nstate = 1; }
+        while (nstate == 1 || nstate == 2) advance();
+        sDesc[0] = nstate == 3 ? nitem : -1;
+        sDesc[1] = nj; sDesc[2] = nka; sDesc[3] = nkb;
+        nstate = 0;
+      }
       __syncthreads();
-      const int q = sItem;
+      const int item = sDesc[0], j = sDesc[1], ka = sDesc[2], kb = sDesc[3];
       __syncthreads();
-      if (q >= nact) break;
-      const int item = a.list[cl][q];
-      const int j = a.item_inst[item];
-      if (*(volatile int *)&a.stop[j]) continue;
-      const int ka = a.item_a[item], kb = a.item_b[item];
+      if (item < 0) break;
+      // No stop check: the flags change only in the pass between iterations, and the compaction
+      // that follows it removes the items of stopped instances from the active list.
       const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j], n = nx + nu;
       const int g = bl_group(n), S = a.grp[j], P = S - 1;
       const int nP = bl_pad4(n), rec = bl_rec(n), nb = bl_nb(n), D = bl_diags(nb);
@@ -217,8 +242,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       T *scr = sm + R.scr + grp * 5 * nP;
       T *sY = scr, *sW = scr + nP, *sQ = scr + 2 * nP, *sT = scr + 3 * nP, *sDU = scr + 4 * nP;
       T *rB = sm;
-      const T *rIc = sm + R.rawI, *rIp = sm + R.rawI + R.capI;
-      T *hB = sm + R.haloB, *hI = sm + R.haloI;
+      T *hB = sm + R.haloB;
       const T *ltiB = hB;  // stage-invariant: block 0 (H_k, k < N-1) then block 1 (H_{N-1})
       T *sQd = sm + R.prm, *sLo = sQd + nP, *sHi = sLo + nP;
       T cacc = (T)0;
@@ -231,35 +255,22 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         sHi[c] = in ? hi[c] : (T)0;
       }
 
-      // Copies of the sub-chunk that starts at stage k0 (thread 0 issues).
+      // Copies of the sub-chunk that starts at stage k0 (thread 0 issues): the stage blocks
+      // (stage-invariant instances: both blocks, once per item). A sub-chunk with nothing to
+      // copy completes its phase with the arrival alone. (The shared-memory buffer the copies
+      // overwrite was only read, and those reads precede the CTA barrier.)
       auto issue = [&](int k0, bool first) {
         const int cnt = min(P, kb - k0);
         const int la = (k0 + cnt < N) ? 1 : 0;  // the next stage: its G and e only
-        const int ns = cnt + la;
         const bool halo = first && ka > 0;
-        const uint32_t it_bytes = (uint32_t)(ns * rec * TS);
         const uint32_t blk_bytes = (uint32_t)((cnt * W + la * oH) * TS);
-        uint32_t bytes = it_bytes * (use_prev ? 2u : 1u);
+        uint32_t bytes = 0u;
         if (!lti) bytes += blk_bytes;
-        if (halo) {
-          bytes += (uint32_t)(rec * TS) * (use_prev ? 2u : 1u);
-          if (!lti) bytes += (uint32_t)(symW * TS);
-        }
+        if (halo && !lti) bytes += (uint32_t)(symW * TS);
         if (lti && first) bytes += (uint32_t)(2 * W * TS);
-        // The iterates the copies read were written through the generic proxy by other CTAs
-        // before the grid barrier: one proxy fence after that barrier, i.e. at the item's first
-        // copy, orders them before every later copy of the item. (The shared-memory buffer the
-        // copies overwrite was only read, and those reads precede the CTA barrier.)
-        if (first) fence_proxy_async();
         mbar_expect_tx(&mbar, bytes);
         if (!lti) bulk_load(rB, blk + (int64_t)k0 * W, blk_bytes, &mbar);
-        bulk_load(sm + R.rawI, Ic + (int64_t)k0 * rec, it_bytes, &mbar);
-        if (use_prev) bulk_load(sm + R.rawI + R.capI, Ip + (int64_t)k0 * rec, it_bytes, &mbar);
-        if (halo) {
-          if (!lti) bulk_load(hB, blk + (int64_t)(ka - 1) * W + oH, (uint32_t)(symW * TS), &mbar);
-          bulk_load(hI, Ic + (int64_t)(ka - 1) * rec, (uint32_t)(rec * TS), &mbar);
-          if (use_prev) bulk_load(hI + rec, Ip + (int64_t)(ka - 1) * rec, (uint32_t)(rec * TS), &mbar);
-        }
+        if (halo && !lti) bulk_load(hB, blk + (int64_t)(ka - 1) * W + oH, (uint32_t)(symW * TS), &mbar);
         if (lti && first) bulk_load(hB, blk, (uint32_t)(2 * W * TS), &mbar);
       };
 
@@ -286,8 +297,8 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           pend = true;
         }
         if (tid == 0 && sc + 1 < nsub) prefetch(k0 + P);
-        // The reference of this group's stage (needed in phase 2) does not come with the copies:
-        // its loads are issued before the wait.
+        // The reference of this group's stage (needed in phase 2) and the hats (phase 1 onwards)
+        // do not come with the copies: their loads are issued before the wait.
         const int k = k0 + grp;
         V4<T> rf4 = zero4<T>();
         if (ref && grp < cnt && own) {
@@ -295,6 +306,17 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
 #pragma unroll
           for (int i = 0; i < 4; ++i)
             if (c0 + i < n) rf4.v[i] = rk[c0 + i];
+        }
+        V4<T> zh = zero4<T>(), vh = zero4<T>(), th = zero4<T>(), bh = zero4<T>(), lh = zero4<T>();
+        if ((grp < cnt || (grp == cnt && la)) && own) {
+          const T *hc = Ic + (int64_t)k * rec + c0, *hp = Ip + (int64_t)k * rec + c0;
+          zh = hat4(hc, hp, use_prev, f);
+          vh = hat4(hc + nP, hp + nP, use_prev, f);
+          lh = hat4(hc + 4 * nP, hp + 4 * nP, use_prev, f);
+          if (grp < cnt) {
+            th = hat4(hc + 2 * nP, hp + 2 * nP, use_prev, f);
+            bh = hat4(hc + 3 * nP, hp + 3 * nP, use_prev, f);
+          }
         }
         // Every thread waits on the copies itself (bounded), so no CTA barrier is needed here;
         // a timeout seen by any thread ends the item for the whole CTA at the barrier after
@@ -306,25 +328,20 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         } else {
           ok = false;  // the copy may still be in flight: it stays pending for the exit wait
         }
+        if (tid == 0 && sc == nsub - 1 && nstate == 0) {
+          nq = atomicAdd(&ctl->queue[it & 1], 1);  // the next item's slot; used after the barrier
+          nstate = 1;
+        }
         T *Xc = sm + R.X + (sc & 1) * S * nP;
         T *Xn = sm + R.X + ((sc & 1) ^ 1) * S * nP;
         const bool stage = arrived && grp < cnt;           // stage k of this sub-chunk
         const bool look = arrived && grp == cnt && la;     // the next stage: q only
         const bool hgrp = arrived && sc == 0 && ka > 0 && grp == S - 1;  // recomputes xbar_a
         const T *Gk = lti ? ltiB : rB + grp * W;
-        const T *hc = rIc + grp * rec, *hp = rIp + grp * rec;
 
-        // ---- phase 1: hats, y and w; q and t in one pass over G_k; du = M t ----
-        V4<T> zh = zero4<T>(), vh = zero4<T>(), th = zero4<T>(), bh = zero4<T>(), lh = zero4<T>();
+        // ---- phase 1: y and w from the hats; q and t in one pass over G_k; du = M t ----
         V4<T> e4 = zero4<T>(), y4 = zero4<T>(), w4 = zero4<T>();
         if ((stage || look) && own) {
-          zh = hat4(hc + c0, hp + c0, use_prev, f);
-          vh = hat4(hc + nP + c0, hp + nP + c0, use_prev, f);
-          lh = hat4(hc + 4 * nP + c0, hp + 4 * nP + c0, use_prev, f);
-          if (stage) {
-            th = hat4(hc + 2 * nP + c0, hp + 2 * nP + c0, use_prev, f);
-            bh = hat4(hc + 3 * nP + c0, hp + 3 * nP + c0, use_prev, f);
-          }
           if (c0 < nx) e4 = ld4(Gk + oE + c0);  // zero beyond nx (padding)
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -376,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         if (stage)
           for (int jj = l; jj < nu; jj += g) sDU[nx + jj] = sym_wrapped(Gk + oM, sT + nx, nu, jj);
         if (!__syncthreads_and(arrived)) { ok = false; break; }  // uniform across the CTA
+        if (tid == 0) advance();
 
         // ---- phase 2: h_k (with q_{k+1} of the next group) and xbar_{k+1} = H_k h_k ----
         if (stage && own) {
@@ -389,8 +407,9 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           st4(sY + c0, h);
         }
         if (hgrp && own) {  // h_{a-1} from the halo hats and q_a (group 0)
-          const V4<T> zm = hat4(hI + c0, hI + rec + c0, use_prev, f);
-          const V4<T> tm = hat4(hI + 2 * nP + c0, hI + rec + 2 * nP + c0, use_prev, f);
+          const T *hm = Ic + (int64_t)(ka - 1) * rec + c0, *pm = Ip + (int64_t)(ka - 1) * rec + c0;
+          const V4<T> zm = hat4(hm, pm, use_prev, f);
+          const V4<T> tm = hat4(hm + 2 * nP, pm + 2 * nP, use_prev, f);
           const V4<T> qa = ld4(sm + R.scr + 2 * nP + c0);
           const V4<T> qd4 = ld4(sQd + c0);
           V4<T> h;
@@ -415,6 +434,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
           }
         }
         __syncthreads();
+        if (tid == 0) advance();
 
         // ---- phase 3: Abar xbar_k and B du by rows; steps 2-4 on the owned components ----
         if (stage) {
@@ -502,18 +522,19 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       }
       if (!ok) break;
 
-      // ---- step 4: this item's share of c; the last item of the instance applies steps 5-7 ----
+      // ---- step 4: this item's share of c (steps 5-7 follow in the pass after the barrier) ----
       for (int off = 16; off > 0; off >>= 1) cacc += __shfl_xor_sync(0xffffffffu, cacc, off);
       if ((tid & 31) == 0) sRed[tid >> 5] = (double)cacc;
       __syncthreads();
       if (tid == 0) {
         double part = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) part += sRed[w];
-        ls::finish_item(a, j, it, part);
+        a.cpart[item] = part;  // steps 5-7 run in the pass after the barrier
       }
     }
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk)) break;
   }

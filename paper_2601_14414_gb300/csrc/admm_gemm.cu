@@ -16,8 +16,8 @@
 // low on this part.)
 //
 // Work items are runs of consecutive stage blocks (LB stages each) of one instance, in the
-// lock-step frame of lockstep.cuh (grid barrier between iterations, steps 5-7 by the CTA
-// finishing the instance's last item). A block reads the hats of one stage more on each side
+// lock-step frame of lockstep.cuh (grid barrier between iterations, steps 5-7 in the pass over
+// the instances after it). A block reads the hats of one stage more on each side
 // (the xbar of its first stage is recomputed from stage a-1, the y of its last stage needs stage
 // b), so items of one iteration are independent. The instance's matrices are expanded from the
 // stage block into shared memory once per item (from L2: they are shared by all items of the
@@ -307,11 +307,12 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(Args<T> a, GemmPlan 
       if (tid == 0) {
         double part = 0.0;
         for (int w2 = 0; w2 < (nthreads >> 5); ++w2) part += sRed[w2];
-        ls::finish_item(a, j, it, part);
+        a.cpart[item] = part;  // steps 5-7 run in the pass after the barrier
       }
     }
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk)) break;
   }

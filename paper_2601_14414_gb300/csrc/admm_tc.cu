@@ -556,19 +556,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
       }
       if (*(volatile int *)&sFail) { ok = false; break; }
 
-      // ---- step 4: this item's share of c; the last item of the instance applies steps 5-7 ----
+      // ---- step 4: this item's share of c (steps 5-7 follow in the pass after the barrier) ----
       for (int off = 16; off > 0; off >>= 1) cacc += __shfl_xor_sync(0xffffffffu, cacc, off);
       if (lane == 0) sRed[warp] = (double)cacc;
       __syncthreads();
       if (tid == 0) {
         double part = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) part += sRed[w];
-        ls::finish_item(a, j, it, part);
+        a.cpart[item] = part;  // steps 5-7 run in the pass after the barrier
       }
     }
     if (!ok) break;
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk)) break;
   }

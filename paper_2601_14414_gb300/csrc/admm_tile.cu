@@ -380,12 +380,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(Args<T> a) {
       if (tid == 0) {
         double part = 0.0;
         for (int w = 0; w < kTileWarps; ++w) part += sRed[w];
-        ls::finish_item(a, j, it, part);
+        a.cpart[item] = part;  // steps 5-7 run in the pass after the barrier
       }
     }
     if (!ok) break;
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk)) break;
   }

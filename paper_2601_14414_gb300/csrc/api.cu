@@ -108,7 +108,8 @@ void free_layout(pimpc_solver *s) {
   s->lay_allocs.clear();
   s->blk_T = nullptr;
   for (int b = 0; b < 3; ++b) s->it[b] = nullptr;
-  s->item_inst = s->item_a = s->item_b = s->list0 = s->list1 = nullptr;
+  s->item_inst = s->item_a = s->item_b = s->list0 = s->list1 = s->item_first = nullptr;
+  s->cpart = nullptr;
 }
 
 template <typename P>
@@ -563,6 +564,17 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     }
   }
   const int nall = (int)item_inst.size();
+  // The items of an instance are consecutive (coarse ones, then fine ones): the per-iteration
+  // finish pass sums an instance's shares of c over [first, first + count).
+  std::vector<int> item_first(2 * batch, 0);
+  for (int i = nall - 1; i >= 0; --i) item_first[item_inst[i] + (i >= nitems ? batch : 0)] = i;
+  for (int i = 0; i < nall; ++i) {
+    const int j = item_inst[i], f = i >= nitems ? batch : 0;
+    if (i >= item_first[j + f] + nitems_inst[j + f]) {
+      why = "internal: the items of an instance are not consecutive";
+      return PIMPC_EINVAL;
+    }
+  }
 
   // (Re)allocate and upload what depends on the schedule.
   cudaDeviceSynchronize();
@@ -579,6 +591,8 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(lalloc(s, &s->item_b, sizeof(int) * nall));
   chk(lalloc(s, &s->list0, sizeof(int) * nall));
   chk(lalloc(s, &s->list1, sizeof(int) * nall));
+  chk(lalloc(s, &s->item_first, sizeof(int) * 2 * batch));
+  chk(lalloc(s, &s->cpart, sizeof(double) * nall));
   chk(lalloc(s, &d_blk, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_Ni, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_W, sizeof(int) * batch));
@@ -601,6 +615,8 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(cudaMemcpy(s->item_a, item_a.data(), sizeof(int) * nall, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(s->item_b, item_b.data(), sizeof(int) * nall, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(s->nitems_inst, nitems_inst.data(), sizeof(int) * 2 * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(s->item_first, item_first.data(), sizeof(int) * 2 * batch, cudaMemcpyHostToDevice));
+  chk(cudaMemset(s->cpart, 0, sizeof(double) * nall));
   chk(cudaMemcpy(d_blk, blk.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_Ni, Ni.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_W, W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
@@ -668,6 +684,7 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.mask = s->mask; a.mask_len = s->mask_len;
   a.item_inst = s->item_inst; a.item_a = s->item_a; a.item_b = s->item_b;
   a.nitems_inst = s->nitems_inst; a.nitems = s->nitems;
+  a.item_first = s->item_first; a.cpart = s->cpart;
   a.list0 = s->list0; a.list1 = s->list1; a.ctl = s->ctl;
   a.base = s->base; a.old_base = s->old_base; a.st = s->st;
   a.alpha = s->alpha; a.cprev = s->cprev; a.coef = s->coef; a.cacc = s->cacc;

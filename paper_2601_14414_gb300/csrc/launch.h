@@ -24,6 +24,10 @@ struct AdmmLaunch {
   // work items
   const int *item_inst, *item_a, *item_b, *nitems_inst;
   int nitems;
+  // per instance the first coarse and the first fine item ([2 batch]; null: c accumulates by
+  // atomics in finish_item), and the per-item shares of c of the current iteration
+  const int *item_first;
+  double *cpart;
   // fine items (one sub-chunk each) after the nitems coarse ones: nfine of them from index
   // nfine_base; nitems_inst holds the coarse then the fine per-instance counts (0: none)
   int nfine_base, nfine, fine_switch;

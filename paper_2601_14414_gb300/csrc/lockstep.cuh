@@ -2,9 +2,10 @@
 //
 // One cooperative launch runs every iteration of every instance. In iteration i each CTA pulls
 // work items (instance j, stage range) from a queue and runs the iteration on them; a bounded
-// grid barrier separates iterations. The CTA that finishes the last item of an instance applies
-// Algorithm 1 steps 5-7 for it (stop test, momentum or restart); stopped instances leave the
-// queue by stream compaction after the barrier.
+// grid barrier separates iterations. Each item stores its share of c^{i+1}; after the barrier a
+// pass over the instances still iterating (one thread each) sums the shares and applies
+// Algorithm 1 steps 5-7 (stop test, momentum or restart), and a second barrier publishes the
+// decisions; stopped instances then leave the queue by stream compaction.
 #pragma once
 #include <math.h>
 
@@ -30,6 +31,9 @@ struct Args {
   const int *item_inst, *item_a, *item_b;
   int nitems;
   const int *nitems_inst;   // [batch] coarse counts, then [batch] fine counts
+  const int *item_first;    // [batch] first coarse item, then [batch] first fine item (null:
+                            // the items accumulate c through finish_item instead)
+  double *cpart;            // [items] each item's share of c^{i+1} in the current iteration
   int nfine_base, nfine;    // fine items: nfine of them from nfine_base (0: none)
   int fine_switch;          // switch to them below fine_switch x grid active coarse items
   int *list[2];
@@ -136,18 +140,10 @@ __device__ inline bool stalled(const Args<T> &a, int j, int it, double c) {
   return (double)(it - a.itbest[j]) >= win;
 }
 
-// Step 4's reduction is finished by the caller; this adds the item's share of c^{i+1} and, for
-// the instance's last item of the iteration, applies steps 5-7. Called by one thread.
+// Steps 5-7 of instance j given the sum s of its squared step-4 terms (c^{i+1} = rho s): the stop
+// tests, then the momentum decision and factor. Called by one thread.
 template <typename T>
-__device__ inline void finish_item(const Args<T> &a, int j, int it, double part) {
-  atomicAdd(&a.cacc[j], part);
-  __threadfence();
-  const int done = atomicAdd(&a.ndone[j], 1);
-  const int fine = *(volatile int *)&a.ctl->fine;
-  if (done != a.nitems_inst[j + (fine ? a.L.batch : 0)] - 1) return;
-  __threadfence();
-  const double s = __longlong_as_double((long long)atomicExch((unsigned long long *)&a.cacc[j], 0ull));
-  a.ndone[j] = 0;
+__device__ inline void apply_steps(const Args<T> &a, int j, int it, double s) {
   const double c = a.rho * s;
   InstState &st = a.st[j];
   st.iters = it + 1;
@@ -185,6 +181,41 @@ __device__ inline void finish_item(const Args<T> &a, int j, int it, double part)
     atomicSub(&a.ctl->active, 1);
     atomicExch(&a.ctl->stopped, 1);
   }
+}
+
+// Step 4's reduction is finished by the caller; this adds the item's share of c^{i+1} and, for
+// the instance's last item of the iteration, applies steps 5-7. Called by one thread.
+template <typename T>
+__device__ inline void finish_item(const Args<T> &a, int j, int it, double part) {
+  atomicAdd(&a.cacc[j], part);
+  __threadfence();
+  const int done = atomicAdd(&a.ndone[j], 1);
+  const int fine = *(volatile int *)&a.ctl->fine;
+  if (done != a.nitems_inst[j + (fine ? a.L.batch : 0)] - 1) return;
+  __threadfence();
+  const double s = __longlong_as_double((long long)atomicExch((unsigned long long *)&a.cacc[j], 0ull));
+  a.ndone[j] = 0;
+  apply_steps(a, j, it, s);
+}
+
+// After the iteration's grid barrier: steps 5-7 for every instance still iterating, from the
+// shares of c^{i+1} its items stored in cpart (summed in item order, so c does not depend on
+// which CTA finished last), then a grid barrier so that every CTA sees the decisions (stop,
+// momentum factor) before the next iteration. The items themselves only store their share:
+// no atomics or fences on the item path. Every item of an instance still iterating runs in
+// every iteration (the active list holds all of them), so the shares are complete.
+template <typename T>
+__device__ inline bool finish_pass(const Args<T> &a, int it, unsigned nblocks, int *sOk) {
+  const int off = *(volatile int *)&a.ctl->fine ? a.L.batch : 0;
+  const int stride = (int)nblocks * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.L.batch; j += stride) {
+    if (*(volatile int *)&a.stop[j]) continue;
+    const int first = a.item_first[j + off], cnt = a.nitems_inst[j + off];
+    double s = 0.0;
+    for (int i = 0; i < cnt; ++i) s += __ldcg(a.cpart + first + i);
+    apply_steps(a, j, it, s);
+  }
+  return grid_sync(a.ctl, nblocks, sOk);
 }
 
 // After the iteration barrier: drop the items of stopped instances from the active list. When
@@ -323,6 +354,7 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.mask = s.mask; a.mask_len = s.mask_len;
   a.item_inst = s.item_inst; a.item_a = s.item_a; a.item_b = s.item_b;
   a.nitems = s.nitems; a.nitems_inst = s.nitems_inst;
+  a.item_first = s.item_first; a.cpart = s.cpart;
   a.nfine_base = s.nfine_base; a.nfine = s.nfine; a.fine_switch = s.fine_switch;
   a.list[0] = s.list0; a.list[1] = s.list1;
   a.ctl = s.ctl;

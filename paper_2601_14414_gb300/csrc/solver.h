@@ -33,6 +33,8 @@ struct pimpc_solver {
   int *ndone = nullptr, *stop = nullptr;
   int *item_inst = nullptr, *item_a = nullptr, *item_b = nullptr, *nitems_inst = nullptr;
   int *list0 = nullptr, *list1 = nullptr;
+  int *item_first = nullptr;  // [2 batch] first coarse / fine item of each instance
+  double *cpart = nullptr;    // [items] per-item share of c of the current iteration
   pimpc::Ctl *ctl = nullptr;
   int64_t *d_bbase = nullptr;
   pimpc::InstState *st = nullptr;

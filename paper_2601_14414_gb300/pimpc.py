@@ -255,6 +255,7 @@ def pimpc_solve_static(nx, nu, N, precision, A, B, e, q, r, xmin, xmax, umin, um
 
 
 FAMILY_LANES, FAMILY_TILES, FAMILY_RESIDENT, FAMILY_CONTRACTION, FAMILY_BLOCKED = 0, 2, 3, 4, 5
+FAMILY_TENSOR, FAMILY_TEMPORAL = 6, 7
 
 
 def pimpc_set_graph(h, enable):

@@ -35,23 +35,28 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     csrc.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
     src = csrc / "admm_blk.cu"
-    src.write_text("// kernel source\n")
-    h = hashlib.sha256(src.read_bytes())
-    for name in bench.KERNEL_HEADERS:                     # headers compiled into the kernel
-        (csrc / name).write_text(f"// {name}\n")
+    src.write_text('// kernel source\n#include "lockstep.cuh"\n#include <math.h>\n')
+    (csrc / "lockstep.cuh").write_text('// lockstep.cuh\n#include "launch.h"\n')
+    (csrc / "launch.h").write_text("// launch.h\n")
+    (csrc / "tc.cuh").write_text("// tc.cuh\n")                # not included by the kernel
+    monkeypatch.setattr(bench, "HERE", str(tmp_path))
+    assert bench.kernel_files("admm_blk.cu") == ["admm_blk.cu", "launch.h", "lockstep.cuh"]
+    h = hashlib.sha256()
+    for name in ("admm_blk.cu", "launch.h", "lockstep.cuh"):
         h.update((csrc / name).read_bytes())
     digest = h.hexdigest()[:16]
     prof = tmp_path / "profiles" / "blk_kernel_f32_batched_512x30.md"
     prof.write_text(f"traffic_per_algorithmic_byte: 1.2345\n\nadmm_blk.cu sha256[:16]: {digest} (x)\n")
-    monkeypatch.setattr(bench, "HERE", str(tmp_path))
     assert bench.profiled_traffic(5) == 1.2345
     assert bench.profiled_traffic(7) is None            # no summary for that family
-    (csrc / "lockstep.cuh").write_text("// changed\n")    # a header changed since the capture
-    assert bench.profiled_traffic(5) is None
-    (csrc / "lockstep.cuh").write_text("// lockstep.cuh\n")
+    (csrc / "tc.cuh").write_text("// changed\n")          # a header the kernel does not include
     assert bench.profiled_traffic(5) == 1.2345
-    src.write_text("// kernel source, changed\n")        # the kernel changed since the capture
+    (csrc / "launch.h").write_text("// changed\n")        # an included header (through another)
     assert bench.profiled_traffic(5) is None
+    (csrc / "launch.h").write_text("// launch.h\n")
+    assert bench.profiled_traffic(5) == 1.2345
+    src.write_text('// kernel source, changed\n#include "lockstep.cuh"\n#include <math.h>\n')
+    assert bench.profiled_traffic(5) is None            # the kernel changed since the capture
 
 
 def test_committed_summaries_name_their_source_and_ratio():

@@ -102,7 +102,10 @@ def test_schedule_errors_keep_the_previous_schedule():
     assert e.value.code == pimpc.EINVAL
     assert s.schedule() == before
     with pytest.raises(pimpc.PimpcError):
-        s.set_schedule(7)
+        s.set_schedule(8)                         # no such family
+    with pytest.raises(pimpc.PimpcError):
+        s.set_schedule(6)                         # tensor cores: stage-invariant FP32 only
+    assert s.schedule() == before
     o = oracle.solve(insts[0], eps=-1.0, max_iters=50, accel=0)
     r = s.solve()
     assert relerr(r["u"][0], o["u"]) <= 1e-10
@@ -113,7 +116,7 @@ def test_autotune_picks_a_schedule_that_solves_correctly(tmp_path):
     s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=150, accel=0)
     pick = s.autotune(trial_iters=10, cache=str(tmp_path / "tune.json"))
     assert pick["family"] in (pimpc.FAMILY_LANES, pimpc.FAMILY_TILES, pimpc.FAMILY_RESIDENT,
-                              pimpc.FAMILY_BLOCKED) and pick["ms"] > 0
+                              pimpc.FAMILY_BLOCKED, pimpc.FAMILY_TEMPORAL) and pick["ms"] > 0
     assert s.schedule()["family"] == pick["family"] and not pick["cached"]
     again = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=150, accel=0)
     assert again.autotune(cache=str(tmp_path / "tune.json"))["cached"]
