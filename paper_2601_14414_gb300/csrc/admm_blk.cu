@@ -141,6 +141,68 @@ __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int
   return acc;
 }
 
+// Abar xbar and B du of the rows r = l, l + g, ... < nx of G (stride ldg) with the block count a
+// compile-time constant; x and du (4 NB values, du zero outside the input blocks from jx on) in
+// shared memory. Row r's two sums go to ax[r] and bd[r].
+template <typename T, int NB>
+__device__ __forceinline__ void rows_t(const T *G, int ldg, const T *x, const T *du, int jx, int l,
+                                       int g, int nx, T *ax, T *bd) {
+  for (int r = l; r < nx; r += g) {
+    const T *row = G + r * ldg;
+    V4<T> sa = zero4<T>(), sb = zero4<T>();
+#pragma unroll
+    for (int J = 0; J < NB; ++J) {
+      const V4<T> gr = ld4(row + 4 * J), xv = ld4(x + 4 * J);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sa.v[i] += gr.v[i] * xv.v[i];
+      if (J >= jx) {
+        const V4<T> dv = ld4(du + 4 * J);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sb.v[i] += gr.v[i] * dv.v[i];
+      }
+    }
+    ax[r] = (sa.v[0] + sa.v[1]) + (sa.v[2] + sa.v[3]);
+    bd[r] = (sb.v[0] + sb.v[1]) + (sb.v[2] + sb.v[3]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void rows_rt(const T *G, int ldg, const T *x, const T *du, int jx,
+                                        int l, int g, int nx, int nb, T *ax, T *bd) {
+  for (int r = l; r < nx; r += g) {
+    const T *row = G + r * ldg;
+    V4<T> sa = zero4<T>(), sb = zero4<T>();
+    for (int J = 0; J < nb; ++J) {
+      const V4<T> gr = ld4(row + 4 * J), xv = ld4(x + 4 * J);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sa.v[i] += gr.v[i] * xv.v[i];
+      if (J >= jx) {
+        const V4<T> dv = ld4(du + 4 * J);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sb.v[i] += gr.v[i] * dv.v[i];
+      }
+    }
+    ax[r] = (sa.v[0] + sa.v[1]) + (sa.v[2] + sa.v[3]);
+    bd[r] = (sb.v[0] + sb.v[1]) + (sb.v[2] + sb.v[3]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void rows(const T *G, int ldg, const T *x, const T *du, int jx, int l,
+                                     int g, int nx, int nb, T *ax, T *bd) {
+  switch (nb) {
+    case 1: rows_t<T, 1>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    case 2: rows_t<T, 2>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    case 3: rows_t<T, 3>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    case 4: rows_t<T, 4>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    case 5: rows_t<T, 5>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    case 6: rows_t<T, 6>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    case 7: rows_t<T, 7>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    case 8: rows_t<T, 8>(G, ldg, x, du, jx, l, g, nx, ax, bd); break;
+    default: rows_rt(G, ldg, x, du, jx, l, g, nx, nb, ax, bd); break;
+  }
+}
+
 template <typename T>
 __device__ inline T clampv(T x, T lo, T hi) {
   return x < lo ? lo : (x > hi ? hi : x);
@@ -437,26 +499,8 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         if (tid == 0) advance();
 
         // ---- phase 3: Abar xbar_k and B du by rows; steps 2-4 on the owned components ----
-        if (stage) {
-          const T *xk = Xc + grp * nP;
-          const int jx = nx >> 2;  // first column block that holds input columns
-          for (int r = l; r < nx; r += g) {
-            const T *row = Gk + r * ldg;
-            V4<T> ax = zero4<T>(), bd = zero4<T>();
-            for (int J = 0; J < nb; ++J) {
-              const V4<T> gr = ld4(row + 4 * J), xv = ld4(xk + 4 * J);
-#pragma unroll
-              for (int i = 0; i < 4; ++i) ax.v[i] += gr.v[i] * xv.v[i];
-              if (J >= jx) {
-                const V4<T> dv = ld4(sDU + 4 * J);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) bd.v[i] += gr.v[i] * dv.v[i];
-              }
-            }
-            sY[r] = (ax.v[0] + ax.v[1]) + (ax.v[2] + ax.v[3]);
-            sW[r] = (bd.v[0] + bd.v[1]) + (bd.v[2] + bd.v[3]);
-          }
-        }
+        if (stage)  // jx = nx / 4: the first column block that holds input columns
+          rows(Gk, ldg, Xc + grp * nP, sDU, nx >> 2, l, g, nx, nb, sY, sW);
         __syncwarp();
         {
           // w of the owned components (stage && own), the input part projected onto a non-box

@@ -109,6 +109,7 @@ void free_layout(pimpc_solver *s) {
   s->blk_T = nullptr;
   for (int b = 0; b < 3; ++b) s->it[b] = nullptr;
   s->item_inst = s->item_a = s->item_b = s->list0 = s->list1 = s->item_first = nullptr;
+  s->list_init = s->ccount = nullptr;
   s->cpart = nullptr;
 }
 
@@ -575,6 +576,19 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
       return PIMPC_EINVAL;
     }
   }
+  // The active list starts with the coarse items longest first (streamed volume), so that the
+  // queue hands out the long items first and the short ones fill the end of the iteration.
+  std::vector<int> list_init(nitems);
+  std::iota(list_init.begin(), list_init.end(), 0);
+  {
+    std::vector<double> icost(nitems);
+    for (int i = 0; i < nitems; ++i) {
+      const int j = item_inst[i];
+      icost[i] = cost[j] / (double)N[j] * (double)(item_b[i] - item_a[i]);
+    }
+    std::stable_sort(list_init.begin(), list_init.end(),
+                     [&](int x, int y) { return icost[x] > icost[y]; });
+  }
 
   // (Re)allocate and upload what depends on the schedule.
   cudaDeviceSynchronize();
@@ -593,6 +607,8 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(lalloc(s, &s->list1, sizeof(int) * nall));
   chk(lalloc(s, &s->item_first, sizeof(int) * 2 * batch));
   chk(lalloc(s, &s->cpart, sizeof(double) * nall));
+  chk(lalloc(s, &s->list_init, sizeof(int) * std::max(nitems, 1)));
+  chk(lalloc(s, &s->ccount, sizeof(int) * std::max(grid, 1)));
   chk(lalloc(s, &d_blk, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_Ni, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_W, sizeof(int) * batch));
@@ -617,6 +633,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(cudaMemcpy(s->nitems_inst, nitems_inst.data(), sizeof(int) * 2 * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(s->item_first, item_first.data(), sizeof(int) * 2 * batch, cudaMemcpyHostToDevice));
   chk(cudaMemset(s->cpart, 0, sizeof(double) * nall));
+  chk(cudaMemcpy(s->list_init, list_init.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_blk, blk.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_Ni, Ni.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_W, W.data(), sizeof(int) * batch, cudaMemcpyHostToDevice));
@@ -685,6 +702,7 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.item_inst = s->item_inst; a.item_a = s->item_a; a.item_b = s->item_b;
   a.nitems_inst = s->nitems_inst; a.nitems = s->nitems;
   a.item_first = s->item_first; a.cpart = s->cpart;
+  a.list_init = s->list_init; a.ccount = s->ccount;
   a.list0 = s->list0; a.list1 = s->list1; a.ctl = s->ctl;
   a.base = s->base; a.old_base = s->old_base; a.st = s->st;
   a.alpha = s->alpha; a.cprev = s->cprev; a.coef = s->coef; a.cacc = s->cacc;

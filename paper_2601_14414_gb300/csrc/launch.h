@@ -28,6 +28,10 @@ struct AdmmLaunch {
   // atomics in finish_item), and the per-item shares of c of the current iteration
   const int *item_first;
   double *cpart;
+  // the active list's starting order (longest items first) and the per-CTA counts of the
+  // order-keeping compaction (null: item order, and a compaction that keeps no order)
+  const int *list_init;
+  int *ccount;
   // fine items (one sub-chunk each) after the nitems coarse ones: nfine of them from index
   // nfine_base; nitems_inst holds the coarse then the fine per-instance counts (0: none)
   int nfine_base, nfine, fine_switch;

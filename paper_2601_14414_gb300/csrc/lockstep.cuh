@@ -34,6 +34,10 @@ struct Args {
   const int *item_first;    // [batch] first coarse item, then [batch] first fine item (null:
                             // the items accumulate c through finish_item instead)
   double *cpart;            // [items] each item's share of c^{i+1} in the current iteration
+  const int *list_init;     // [coarse items] the starting order of the active list (null:
+                            // item order), longest first
+  int *ccount;              // [grid] per-CTA counts of the order-keeping compaction (null: the
+                            // compaction keeps no order)
   int nfine_base, nfine;    // fine items: nfine of them from nfine_base (0: none)
   int fine_switch;          // switch to them below fine_switch x grid active coarse items
   int *list[2];
@@ -218,6 +222,17 @@ __device__ inline bool finish_pass(const Args<T> &a, int it, unsigned nblocks, i
   return grid_sync(a.ctl, nblocks, sOk);
 }
 
+// Sum over the CTA (every thread gets the total); red holds blockDim.x / 32 ints of scratch.
+__device__ inline int block_sum(int v, int *red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int t = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
 // After the iteration barrier: drop the items of stopped instances from the active list. When
 // the active coarse items no longer cover the grid several times over (few instances left,
 // each item run by one CTA one sub-chunk after the other, the last items of an iteration
@@ -234,18 +249,56 @@ __device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk) {
   if (!*(volatile int *)&ctl->stopped && !go_fine) return true;
   const int src = cl, dst = cl ^ 1;
   const int total = go_fine ? a.nfine : nact;
-  for (int b0 = blockIdx.x * nthreads; b0 < total; b0 += nblocks * nthreads) {
-    const int qi = b0 + tid;
-    int keep = 0, item = 0;
-    if (qi < total) {
-      item = go_fine ? a.nfine_base + qi : a.list[src][qi];
-      keep = *(volatile int *)&a.stop[a.item_inst[item]] == 0;
+  auto entry = [&](int qi, int &item) {  // the qi-th source entry and whether it stays
+    item = go_fine ? a.nfine_base + qi : a.list[src][qi];
+    return *(volatile int *)&a.stop[a.item_inst[item]] == 0;
+  };
+  if (a.ccount) {
+    // Order-keeping: CTA b takes a contiguous range of the source list, counts what stays,
+    // and after a barrier writes it at the sum of the counts of the CTAs before it, so the list
+    // keeps its longest-first order (the queue then hands out the long items first).
+    __shared__ int red[32];
+    const int per = (total + (int)nblocks - 1) / (int)nblocks;
+    const int q0 = min(total, (int)blockIdx.x * per), q1 = min(total, q0 + per);
+    int kept = 0, item;
+    for (int qi = q0 + tid; qi < q1; qi += nthreads) kept += entry(qi, item) ? 1 : 0;
+    kept = block_sum(kept, red);
+    if (tid == 0) a.ccount[blockIdx.x] = kept;
+    if (!grid_sync(ctl, nblocks, sOk)) return false;
+    int before = 0, all = 0;
+    for (int b = tid; b < (int)nblocks; b += nthreads) {
+      const int c = __ldcg(a.ccount + b);
+      all += c;
+      if (b < (int)blockIdx.x) before += c;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    int wbase = 0;
-    if ((tid & 31) == 0 && m) wbase = atomicAdd(&ctl->nlist[dst], __popc(m));
-    wbase = __shfl_sync(0xffffffffu, wbase, 0);
-    if (keep) a.list[dst][wbase + __popc(m & ((1u << (tid & 31)) - 1u))] = item;
+    before = block_sum(before, red);
+    all = block_sum(all, red);
+    for (int c0 = q0; c0 < q1; c0 += nthreads) {
+      const int qi = c0 + tid;
+      const int keep = qi < q1 && entry(qi, item);
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      __syncthreads();
+      if ((tid & 31) == 0) red[tid >> 5] = __popc(m);
+      __syncthreads();
+      int wbase = 0;
+      for (int w = 0; w < (tid >> 5); ++w) wbase += red[w];
+      if (keep) a.list[dst][before + wbase + __popc(m & ((1u << (tid & 31)) - 1u))] = item;
+      int chunk = 0;
+      for (int w = 0; w < (nthreads >> 5); ++w) chunk += red[w];
+      before += chunk;
+    }
+    if (blockIdx.x == 0 && tid == 0) ctl->nlist[dst] = all;
+  } else {
+    for (int b0 = blockIdx.x * nthreads; b0 < total; b0 += nblocks * nthreads) {
+      const int qi = b0 + tid;
+      int keep = 0, item = 0;
+      if (qi < total) keep = entry(qi, item);
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      int wbase = 0;
+      if ((tid & 31) == 0 && m) wbase = atomicAdd(&ctl->nlist[dst], __popc(m));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (keep) a.list[dst][wbase + __popc(m & ((1u << (tid & 31)) - 1u))] = item;
+    }
   }
   if (!grid_sync(ctl, nblocks, sOk)) return false;
   cl = dst;
@@ -278,7 +331,7 @@ __global__ void solve_init_kernel(Args<T> a, int warm) {
     s.iters = 0; s.status = kMaxIter; s.momentum = 0; s.pad = 0; s.c = 0.0;
     a.st[j] = s;
   }
-  if (j < a.nitems) a.list[0][j] = j;
+  if (j < a.nitems) a.list[0][j] = a.list_init ? a.list_init[j] : j;
 }
 
 // Starting iterates: zero (cold start) or the previous solve's iterates shifted one stage.
@@ -355,6 +408,7 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.item_inst = s.item_inst; a.item_a = s.item_a; a.item_b = s.item_b;
   a.nitems = s.nitems; a.nitems_inst = s.nitems_inst;
   a.item_first = s.item_first; a.cpart = s.cpart;
+  a.list_init = s.list_init; a.ccount = s.ccount;
   a.nfine_base = s.nfine_base; a.nfine = s.nfine; a.fine_switch = s.fine_switch;
   a.list[0] = s.list0; a.list[1] = s.list1;
   a.ctl = s.ctl;

@@ -35,6 +35,8 @@ struct pimpc_solver {
   int *list0 = nullptr, *list1 = nullptr;
   int *item_first = nullptr;  // [2 batch] first coarse / fine item of each instance
   double *cpart = nullptr;    // [items] per-item share of c of the current iteration
+  int *list_init = nullptr;   // [coarse items] starting order of the active list
+  int *ccount = nullptr;      // [grid] per-CTA counts of the order-keeping compaction
   pimpc::Ctl *ctl = nullptr;
   int64_t *d_bbase = nullptr;
   pimpc::InstState *st = nullptr;
