@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
-    if (!ls::compact(a, cl, nact, &sOk)) break;
+    if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }
   // Never leave a bulk copy in flight into shared memory: wait (bounded) for pending phases.
   for (int b = 0; b < 2; ++b)

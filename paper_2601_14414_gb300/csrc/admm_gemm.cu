@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(Args<T> a, GemmPlan 
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
-    if (!ls::compact(a, cl, nact, &sOk)) break;
+    if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }
 }
 

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(Args<T> a, TbPlan pl) {
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(blk + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
-    if (!ls::compact(a, cl, nact, &sOk)) break;
+    if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }
 }
 
@@ -290,6 +290,13 @@ int tb_threads() { return kTbThreads; }
 // Shared-memory words of a window of S stages (one instance).
 int64_t tb_window_words(int nx, int nu, int W, int lti, int precision, int S) {
   return tb_regions(nx + nu, W, lti, precision == 0 ? 4 : 8, S).total;
+}
+
+size_t tb_static_smem(int precision) {
+  cudaFuncAttributes fa{};
+  const cudaError_t rc = precision == 0 ? cudaFuncGetAttributes(&fa, tb_kernel<float>)
+                                        : cudaFuncGetAttributes(&fa, tb_kernel<double>);
+  return rc == cudaSuccess ? fa.sharedSizeBytes : 1024;
 }
 
 cudaError_t tb_configure(int precision, size_t smem, int *blocks_per_sm) {

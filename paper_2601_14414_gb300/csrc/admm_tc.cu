@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Args<float> a, const fl
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
-    if (!ls::compact(a, cl, nact, &sOk)) break;
+    if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }
   if (!ok && tid == 0) atomicExch(&ctl->err, 3);
   // Never leave with a copy or an MMA in flight: wait (bounded) for what is still pending.

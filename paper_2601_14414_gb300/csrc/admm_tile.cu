@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(Args<T> a) {
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
-    if (!ls::compact(a, cl, nact, &sOk)) break;
+    if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }
   // Never leave a bulk copy in flight into shared memory: wait (bounded) for a pending phase.
   if (tid == 0 && pend) {

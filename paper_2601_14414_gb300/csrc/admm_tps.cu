@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) tps_kernel(l
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
-    if (!ls::compact(a, cl, nact, &sOk)) break;
+    if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }
 }
 

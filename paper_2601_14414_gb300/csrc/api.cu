@@ -208,8 +208,9 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
     // memory fits the budget of cps CTAs per SM; an instance that fits whole is one closed window.
     const int T = sc.item_scale > 0 ? sc.item_scale : 8;
     const int cps = sc.ctas_per_sm > 0 ? sc.ctas_per_sm : 1;
+    const int64_t stat = (int64_t)tb_static_smem(precision);
     const int64_t budget =
-        std::min<int64_t>((int64_t)smem_sm / cps - 1024 - 256, optin - 256) / 128 * 128;
+        std::min<int64_t>((int64_t)smem_sm / cps - 1024 - stat, optin - stat) / 128 * 128;
     std::vector<int> S(batch), inner(batch);
     for (int j = 0; j < batch; ++j) {
       const int n = nx[j] + nu[j];

@@ -110,6 +110,7 @@ cudaError_t launch_tc(const AdmmLaunch &s, const float *tcm, const int64_t *tc_o
 // Temporal blocking of the plain iteration: windows of stages iterated T times in shared memory.
 int tb_threads();
 int64_t tb_window_words(int nx, int nu, int W, int lti, int precision, int S);
+size_t tb_static_smem(int precision);  // the kernel's static shared memory (bytes)
 cudaError_t tb_configure(int precision, size_t smem, int *blocks_per_sm);
 cudaError_t launch_tb(const AdmmLaunch &s, int precision, int T, size_t smem, cudaStream_t stream);
 

@@ -239,8 +239,10 @@ __device__ inline int block_sum(int v, int *red) {
 // leaving most CTAs idle), the list is rebuilt from the fine items of the active instances
 // instead, so that their sub-chunks spread over the CTAs. Returns false if a barrier
 // failed. Uniform control flow across the grid (every CTA reads the same nact, stopped, fine).
+// red: shared scratch of at least blockDim.x / 32 ints (the kernel's reduction buffer, free
+// between iterations).
 template <typename T>
-__device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk) {
+__device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk, int *red) {
   Ctl *ctl = a.ctl;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const unsigned nblocks = gridDim.x;
@@ -257,7 +259,6 @@ __device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk) {
     // Order-keeping: CTA b takes a contiguous range of the source list, counts what stays,
     // and after a barrier writes it at the sum of the counts of the CTAs before it, so the list
     // keeps its longest-first order (the queue then hands out the long items first).
-    __shared__ int red[32];
     const int per = (total + (int)nblocks - 1) / (int)nblocks;
     const int q0 = min(total, (int)blockIdx.x * per), q1 = min(total, q0 + per);
     int kept = 0, item;

@@ -78,3 +78,19 @@ def test_tb_runs_the_plain_iteration_only():
         s.solve()
     assert e.value.code == pimpc.ESTATE
     s.close()
+
+
+def test_tb_windows_at_the_full_shared_memory_budget():
+    # Every state size of the batched workload with inputs 2, 5 and 8: the widest windows of the
+    # wide instances fill the shared memory of a CTA next to the kernel's static shared memory.
+    dims = [(nx, nu, 60) for nx in range(4, 25) for nu in (2, 5, 8)]
+    insts = batch(8, dims)
+    for T in (4, 8):
+        s = pimpc.Solver(insts, precision=pimpc.F32, eps=-1.0, max_iters=2 * T + 1, accel=0)
+        s.set_schedule(7, 0, T)
+        r = s.solve()
+        ora = oracle.solve_batch(insts, eps=-1.0, max_iters=2 * T + 1, accel=0)
+        for j, o in enumerate(ora):
+            assert relerr(r["u"][j], o["u"]) <= 1e-4, (T, j)
+            assert relerr(r["x"][j], o["x"]) <= 1e-4, (T, j)
+        s.close()
