@@ -10,7 +10,8 @@ then checks what the solve kernel relies on:
   * the per-lane product the kernel runs (per block diagonal: block (I, I+d) against h_{I+d},
     the transpose of block (I-d, I) against h_{I-d}, the middle diagonal of an even nb once)
     reproduces S h;
-  * G rows start 16-byte aligned and 8 consecutive rows start in 8 distinct 16-byte bank
+  * G rows start 16-byte aligned; the FP32 row products (lane l reads row l, in a rotated block
+    order for a power-of-two block count) and 8 consecutive FP64 rows hit distinct 16-byte bank
     groups; every offset inside a block is 16-byte aligned.
 """
 import os
@@ -132,9 +133,21 @@ def test_g_stride_and_offsets(layout):
         nb = L["nb"]
         for ld, word in ((L["ld4"], 4), (L["ld8"], 8)):
             assert ld >= 4 * nb and (ld * word) % 16 == 0
-            units = ld * word // 16                       # 16-byte words per row
-            starts = [(r * units) % 8 for r in range(8)]  # bank group of row r's first word
-            assert len(set(starts)) == 8, (m, word)
+        # FP64: 8 consecutive rows start in 8 distinct 16-byte bank groups
+        units = L["ld8"] * 8 // 16
+        assert len({(r * units) % 8 for r in range(8)}) == 8, m
+        # FP32: the row products (lane l of a group of g lanes reads row l, at step J block J,
+        # or block (J + l) mod nb for a power-of-two nb >= 4) put the lanes of a quarter warp
+        # that belong to one group on distinct 16-byte bank groups at every step
+        units = L["ld4"] * 4 // 16
+        g = 4 if m <= 16 else (8 if m <= 32 else 16)
+        rot = nb >= 4 and nb & (nb - 1) == 0
+        assert L["ld4"] == 4 * nb or L["ld4"] == 4 * (nb + 1), m
+        for J in range(nb):
+            for q0 in range(0, g, 8):
+                lanes = range(q0, min(g, q0 + 8))
+                banks = [(l * units + ((J + l) % nb if rot else J)) % 8 for l in lanes]
+                assert len(set(banks)) == len(banks), (m, J)
     for nx, nu, ts, oE, oH, oM, W, rec in blocks:
         n = nx + nu
         ld = mats[n]["ld4"] if ts == 4 else mats[n]["ld8"]
