@@ -2,11 +2,12 @@
 //
 // For stage k (LTV) the warp forms
 //   K = Qbar + rho I + rho Abar_{k+1}^T Abar_{k+1}   (k < N-1),   K = Qbar + rho I   (k = N-1),
-// where Abar^T Abar = G^T G + diag(0, I_nu) with G = [A | B] (Theorem 2's velocity form), factors
-// K = L L^T (Cholesky) and writes H_k = K^{-1}, obtained column by column from L y = e_c and
-// L^T x = y. It also writes M_k = (B_k^T B_k + I + Wdu / rho)^{-1}, so that the du update of
-// Algorithm 1 step 1, J_k (v - beta) with J_k = (Bbar^T Bbar)^{-1} Bbar^T, is
-// M_k (B_k^T (v - beta)_x + (v - beta)_u); and it copies G_k and e_k into the stage block.
+// where Abar^T Abar = G^T G + diag(0, I_nu) with G = [A | B] (Theorem 2's velocity form), and
+// writes H_k = K^{-1}, inverted by sweeps of the symmetric matrix (Gauss-Jordan elimination in
+// pivot order, which needs no pivoting for a positive definite K). It also writes
+// M_k = (B_k^T B_k + I + Wdu / rho)^{-1}, so that the du update of Algorithm 1 step 1,
+// J_k (v - beta) with J_k = (Bbar^T Bbar)^{-1} Bbar^T, is M_k (B_k^T (v - beta)_x + (v - beta)_u);
+// and it copies G_k and e_k into the stage block.
 // Outputs are converted to the iteration precision T. LTI instances have two blocks: block 0
 // with H = (Qbar + rho I + rho Abar^T Abar)^{-1} and block 1 with the terminal H_{N-1}.
 #include "launch.h"
@@ -28,49 +29,6 @@ struct FactArgs {
   int *err;                  // [batch]: set to 1 for an instance with a non-positive pivot
 };
 
-// Cholesky of the m x m matrix in S (lower triangle used, leading dimension ld) in place;
-// then overwrite X (m x m, column c owned by lane c and c + 32) with S^{-1}. dinv (m words of
-// scratch) receives the reciprocals of the diagonal of L, taken once per column, so that the
-// column scaling and both triangular solves multiply instead of dividing.
-__device__ void chol_inverse(double *S, double *X, double *dinv, int m, int ld, int lane, int *err) {
-  for (int j = 0; j < m; ++j) {
-    __syncwarp();
-    if (lane == 0) {
-      double d = S[j * ld + j];
-      for (int p = 0; p < j; ++p) d -= S[j * ld + p] * S[j * ld + p];
-      if (!(d > 0.0)) { *err = 1; d = 1.0; }
-      const double l = sqrt(d);
-      S[j * ld + j] = l;
-      dinv[j] = 1.0 / l;
-    }
-    __syncwarp();
-    const double r = dinv[j];
-    for (int i = j + 1 + lane; i < m; i += 32) {
-      double s = S[i * ld + j];
-      for (int p = 0; p < j; ++p) s -= S[i * ld + p] * S[j * ld + p];
-      S[i * ld + j] = s * r;
-    }
-  }
-  __syncwarp();
-  for (int c = lane; c < m; c += 32) {
-    // forward: L y = e_c  (y_i = 0 for i < c)
-    for (int i = 0; i < c; ++i) X[i * ld + c] = 0.0;
-    X[c * ld + c] = dinv[c];
-    for (int i = c + 1; i < m; ++i) {
-      double s = 0.0;
-      for (int p = c; p < i; ++p) s += S[i * ld + p] * X[p * ld + c];
-      X[i * ld + c] = -s * dinv[i];
-    }
-    // backward: L^T x = y
-    for (int i = m - 1; i >= 0; --i) {
-      double s = X[i * ld + c];
-      for (int p = i + 1; p < m; ++p) s -= S[p * ld + i] * X[p * ld + c];
-      X[i * ld + c] = s * dinv[i];
-    }
-  }
-  __syncwarp();
-}
-
 // Row i and column c <= i of the t-th lower-triangle entry in row-major order
 // (t = i (i + 1) / 2 + c), so that a warp's lanes take consecutive entries.
 __device__ __forceinline__ void tri_index(int t, int &i, int &c) {
@@ -78,6 +36,52 @@ __device__ __forceinline__ void tri_index(int t, int &i, int &c) {
   while (i * (i + 1) / 2 > t) --i;
   while ((i + 1) * (i + 2) / 2 <= t) ++i;
   c = t - i * (i + 1) / 2;
+}
+
+// The inverse of the symmetric positive definite m x m matrix whose lower triangle is in S
+// (row-major, leading dimension ld), by m sweeps of the symmetric matrix (Gauss-Jordan
+// elimination with the pivots in order; for a positive definite matrix every pivot is positive,
+// and a pivot that is not flags err): sweeping pivot k with d = 1 / a_kk sets a_ij -= a_ik a_kj d
+// for i, j != k, a_ik = a_ik d, a_kk = -d; after all m sweeps the matrix holds -S^{-1}. The lanes
+// share the entries of the lower triangle (t = lane, lane + 32, ... in row-major order), so that
+// every FP64 instruction of a sweep has all 32 lanes busy. X (m x m, leading dimension ld)
+// serves as scratch for the pivot column during the sweeps and receives S^{-1} (both triangles).
+__device__ void sweep_inverse(double *S, double *X, int m, int ld, int lane, int *err) {
+  double *col = X, *cold = X + m;  // column k, and column k times d
+  const int T = m * (m + 1) / 2;
+  int i0 = 0, j0 = 0;
+  if (lane < T) tri_index(lane, i0, j0);
+  for (int k = 0; k < m; ++k) {
+    __syncwarp();
+    double akk = S[k * ld + k];
+    if (!(akk > 0.0)) {
+      if (lane == 0) *err = 1;
+      akk = 1.0;
+    }
+    const double d = 1.0 / akk;
+    for (int i = lane; i < m; i += 32) {
+      const double c = i >= k ? S[i * ld + k] : S[k * ld + i];
+      col[i] = c;
+      cold[i] = c * d;
+    }
+    __syncwarp();
+    int i = i0, j = j0;
+    for (int t = lane; t < T; t += 32) {
+      double v;
+      if (i == k) v = (j == k) ? -d : cold[j];
+      else if (j == k) v = cold[i];
+      else v = fma(-col[i], cold[j], S[i * ld + j]);
+      S[i * ld + j] = v;
+      j += 32;  // the entry 32 further on in row-major order
+      while (j > i) { j -= i + 1; ++i; }
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < m * m; t += 32) {
+    const int r = t / m, c = t - r * m;
+    X[r * ld + c] = -(r >= c ? S[r * ld + c] : S[c * ld + r]);
+  }
+  __syncwarp();
 }
 
 template <typename T>
@@ -128,7 +132,7 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     if (i == c) s += qd[i] + rho;
     S[i * ld + c] = s;
   }
-  chol_inverse(S, X, G, n, ld, lane, a.err + j);  // G is rebuilt below: scratch for 1/L_ii
+  sweep_inverse(S, X, n, ld, lane, a.err + j);
 
   const int W = a.L.W[j];
   const int lay = a.L.tiled;
@@ -216,7 +220,7 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
     S[i * nu + c] = s;
   }
   __syncwarp();
-  chol_inverse(S, X, G, nu, nu, lane, a.err + j);  // G is not read again: scratch for 1/L_ii
+  sweep_inverse(S, X, nu, nu, lane, a.err + j);
   put_sym(oM, nu, X, nu);
   if (!packed) {  // padding of a plain or blocked block
     const int end = oM + wrapped_size(nu);
