@@ -143,12 +143,12 @@ __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int
 
 // Abar xbar and B du of the rows r = l, l + g, ... < nx of G (stride ldg) with the block count a
 // compile-time constant; x and du (4 NB values, du zero outside the input blocks from jx on) in
-// shared memory. Row r's two sums go to ax[r] and bd[r]. For a power-of-two NB >= 4 lane l
-// takes the blocks in the order J + l mod NB (the G stride is then 4 NB words: see bl_ldg).
+// shared memory. Row r's two sums go to ax[r] and bd[r]. For NB = 4 and 8 lane l takes the
+// blocks in the order J + l mod NB (the G stride is then 4 NB words: see bl_ldg, bl_rot).
 template <typename T, int NB>
 __device__ __forceinline__ void rows_t(const T *G, int ldg, const T *x, const T *du, int jx, int l,
                                        int g, int nx, T *ax, T *bd) {
-  constexpr bool kRot = NB >= 4 && (NB & (NB - 1)) == 0;
+  constexpr bool kRot = NB == 4 || NB == 8;
   for (int r = l; r < nx; r += g) {
     const T *row = G + r * ldg;
     V4<T> sa = zero4<T>(), sb = zero4<T>();
@@ -172,12 +172,10 @@ __device__ __forceinline__ void rows_t(const T *G, int ldg, const T *x, const T 
 template <typename T>
 __device__ __forceinline__ void rows_rt(const T *G, int ldg, const T *x, const T *du, int jx,
                                         int l, int g, int nx, int nb, T *ax, T *bd) {
-  const bool rot = bl_rot(nb);
-  for (int r = l; r < nx; r += g) {
+  for (int r = l; r < nx; r += g) {  // nb > 8: odd G stride, blocks in order
     const T *row = G + r * ldg;
     V4<T> sa = zero4<T>(), sb = zero4<T>();
-    for (int Js = 0; Js < nb; ++Js) {
-      const int J = rot ? ((Js + l) & (nb - 1)) : Js;
+    for (int J = 0; J < nb; ++J) {
       const V4<T> gr = ld4(row + 4 * J), xv = ld4(x + 4 * J);
 #pragma unroll
       for (int i = 0; i < 4; ++i) sa.v[i] += gr.v[i] * xv.v[i];

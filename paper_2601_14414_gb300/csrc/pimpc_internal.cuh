@@ -121,20 +121,20 @@ __host__ __device__ inline int halo_copies(int tw, int N, int k, int *tt, int *s
 // reading row a of consecutive blocks read consecutive 16-byte words. The G stride is chosen for
 // the row products, where lane l of a group reads row l: FP32 rows are 4 nb words long when nb
 // is odd (an odd number of 16-byte words: rows l = 0..7 start in distinct 16-byte bank groups)
-// or a power of two (lane l then reads, at step J, block (J + l) mod nb of its row, which again
-// puts eight lanes on distinct bank groups: bl_rot), else 4 (nb + 1) words; FP64 rows are
-// 4 nb + 2 words. Iterates: [z | v | theta | beta | lambda], each padded to 4 (record
+// or 4 or 8 (lane l then reads, at step J, block (J + l) mod nb of its row, which again puts
+// eight lanes on distinct bank groups: bl_rot), else 4 (nb + 1) words; FP64 rows are 4 nb + 2
+// words. Iterates: [z | v | theta | beta | lambda], each padded to 4 (record
 // 5 * bl_pad4(n)).
 __host__ __device__ inline int bl_pad4(int m) { return (m + 3) & ~3; }
 __host__ __device__ inline int bl_nb(int m) { return (m + 3) >> 2; }
 __host__ __device__ inline int bl_diags(int nb) { return nb / 2 + 1; }
 __host__ __device__ inline bool bl_pow2(int nb) { return (nb & (nb - 1)) == 0; }
 // The row products read block (J + l) mod nb at step J on lane l.
-__host__ __device__ inline bool bl_rot(int nb) { return nb >= 4 && bl_pow2(nb); }
+__host__ __device__ inline bool bl_rot(int nb) { return nb == 4 || nb == 8; }
 __host__ __device__ inline int bl_ldg(int n, int tsize) {
   const int nb = bl_nb(n);
   if (tsize != 4) return 4 * nb + 2;
-  return ((nb & 1) || bl_pow2(nb)) ? 4 * nb : 4 * (nb + 1);
+  return ((nb & 1) || nb <= 2 || bl_rot(nb)) ? 4 * nb : 4 * (nb + 1);
 }
 __host__ __device__ inline int bl_sym_words(int m) {
   const int nb = bl_nb(m);

@@ -11,7 +11,7 @@ then checks what the solve kernel relies on:
     the transpose of block (I-d, I) against h_{I-d}, the middle diagonal of an even nb once)
     reproduces S h;
   * G rows start 16-byte aligned; the FP32 row products (lane l reads row l, in a rotated block
-    order for a power-of-two block count) and 8 consecutive FP64 rows hit distinct 16-byte bank
+    order for block counts 4 and 8) and 8 consecutive FP64 rows hit distinct 16-byte bank
     groups; every offset inside a block is 16-byte aligned.
 """
 import os
@@ -137,11 +137,11 @@ def test_g_stride_and_offsets(layout):
         units = L["ld8"] * 8 // 16
         assert len({(r * units) % 8 for r in range(8)}) == 8, m
         # FP32: the row products (lane l of a group of g lanes reads row l, at step J block J,
-        # or block (J + l) mod nb for a power-of-two nb >= 4) put the lanes of a quarter warp
+        # or block (J + l) mod nb for nb = 4 and 8) put the lanes of a quarter warp
         # that belong to one group on distinct 16-byte bank groups at every step
         units = L["ld4"] * 4 // 16
         g = 4 if m <= 16 else (8 if m <= 32 else 16)
-        rot = nb >= 4 and nb & (nb - 1) == 0
+        rot = nb in (4, 8)
         assert L["ld4"] == 4 * nb or L["ld4"] == 4 * (nb + 1), m
         for J in range(nb):
             for q0 in range(0, g, 8):
