@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
       __syncthreads();
       if (q >= nact) break;
       const int item = a.list[cl][q];
+      if (item < 0) continue;  // an entry of an instance that has stopped
       const int j = a.item_inst[item];
       if (*(volatile int *)&a.stop[j]) continue;
       const int ka = a.item_a[item], kb = a.item_b[item];
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(256, 3) admm_kernel(Args<T> a, Smem lay) {
     }
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
-    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, cl, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }

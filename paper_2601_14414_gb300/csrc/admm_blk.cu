@@ -247,8 +247,8 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
   bool pend = false;
   // Thread 0 fetches the next item (queue slot, list entry, item fields: three dependent global
   // reads) during the current item's last sub-chunk, one step per phase, so that it is known
-  // when the item ends. nstate: 0 nothing fetched, 1 slot taken, 2 item known, 3 ready,
-  // 4 the queue is empty.
+  // when the item ends. nstate: 0 nothing fetched, 1 slot taken, 2 entry known, 3 ready (an item,
+  // or -1 for a marked entry), 4 the queue is empty.
   int nstate = 0, nq = 0, nitem = 0, nj = 0, nka = 0, nkb = 0;
 
   int cl = 0;
@@ -259,23 +259,25 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       if (nstate == 1) {
         if (nq < nact) { nitem = a.list[cl][nq]; nstate = 2; } else { nstate = 4; }
       } else if (nstate == 2) {
-        nj = a.item_inst[nitem]; nka = a.item_a[nitem]; nkb = a.item_b[nitem]; nstate = 3;
+        if (nitem >= 0) { nj = a.item_inst[nitem]; nka = a.item_a[nitem]; nkb = a.item_b[nitem]; }
+        nstate = 3;
       }
     };
     for (;;) {
       if (tid == 0) {
         if (nstate == 0) { nq = atomicAdd(&ctl->queue[it & 1], 1); nstate = 1; }
         while (nstate == 1 || nstate == 2) advance();
-        sDesc[0] = nstate == 3 ? nitem : -1;
+        sDesc[0] = nstate == 3 ? nitem : -2;  // -1: an entry of a stopped instance; -2: no more
         sDesc[1] = nj; sDesc[2] = nka; sDesc[3] = nkb;
         nstate = 0;
       }
       __syncthreads();
       const int item = sDesc[0], j = sDesc[1], ka = sDesc[2], kb = sDesc[3];
       __syncthreads();
-      if (item < 0) break;
-      // No stop check: the flags change only in the pass between iterations, and the compaction
-      // that follows it removes the items of stopped instances from the active list.
+      if (item == -2) break;
+      if (item < 0) continue;
+      // No stop check: the flags change only in the pass between iterations, which marks the
+      // list entries of the instances it stops (-1) until a compaction removes them.
       const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j], n = nx + nu;
       const int g = bl_group(n), S = a.grp[j], P = S - 1;
       const int nP = bl_pad4(n), rec = bl_rec(n), nb = bl_nb(n), D = bl_diags(nb);
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
     }
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
-    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, cl, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kTbThreads) tb_kernel(Args<T> a, TbPlan pl) {
       __syncthreads();
       if (q >= nact) break;
       const int item = a.list[cl][q];
+      if (item < 0) continue;  // an entry of an instance that has stopped
       const int j = a.item_inst[item];
       if (*(volatile int *)&a.stop[j]) continue;
       const int ka = a.item_a[item], kb = a.item_b[item];

@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(Args<T> a) {
       __syncthreads();
       if (q >= nact) break;
       const int item = a.list[cl][q];
+      if (item < 0) continue;  // an entry of an instance that has stopped
       const int j = a.item_inst[item];
       if (*(volatile int *)&a.stop[j]) continue;
       const int t0 = a.item_a[item], nt = a.item_b[item] - t0;
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(Args<T> a) {
     if (!ok) break;
     if (blockIdx.x == 0 && tid == 0) ctl->queue[(it + 1) & 1] = 0;
     if (!ls::grid_sync(ctl, nblocks, &sOk)) break;
-    if (!ls::finish_pass(a, it, nblocks, &sOk)) break;
+    if (!ls::finish_pass(a, it, cl, nblocks, &sOk)) break;
     if (*(volatile int *)&ctl->active <= 0) break;
     if (!ls::compact(a, cl, nact, &sOk, reinterpret_cast<int *>(sRed))) break;
   }

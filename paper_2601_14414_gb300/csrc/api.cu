@@ -109,7 +109,7 @@ void free_layout(pimpc_solver *s) {
   s->blk_T = nullptr;
   for (int b = 0; b < 3; ++b) s->it[b] = nullptr;
   s->item_inst = s->item_a = s->item_b = s->list0 = s->list1 = s->item_first = nullptr;
-  s->list_init = s->ccount = nullptr;
+  s->list_init = s->ccount = s->pos_of = nullptr;
   s->cpart = nullptr;
 }
 
@@ -610,6 +610,7 @@ int apply_schedule(pimpc_solver *s, const Schedule &sc_in, std::string &why) {
   chk(lalloc(s, &s->cpart, sizeof(double) * nall));
   chk(lalloc(s, &s->list_init, sizeof(int) * std::max(nitems, 1)));
   chk(lalloc(s, &s->ccount, sizeof(int) * std::max(grid, 1)));
+  chk(lalloc(s, &s->pos_of, sizeof(int) * nall));
   chk(lalloc(s, &d_blk, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_Ni, sizeof(int64_t) * batch));
   chk(lalloc(s, &d_W, sizeof(int) * batch));
@@ -703,7 +704,7 @@ int run_solve(pimpc_solver *s, const double *dx0, const double *dup, const doubl
   a.item_inst = s->item_inst; a.item_a = s->item_a; a.item_b = s->item_b;
   a.nitems_inst = s->nitems_inst; a.nitems = s->nitems;
   a.item_first = s->item_first; a.cpart = s->cpart;
-  a.list_init = s->list_init; a.ccount = s->ccount;
+  a.list_init = s->list_init; a.ccount = s->ccount; a.pos_of = s->pos_of;
   a.list0 = s->list0; a.list1 = s->list1; a.ctl = s->ctl;
   a.base = s->base; a.old_base = s->old_base; a.st = s->st;
   a.alpha = s->alpha; a.cprev = s->cprev; a.coef = s->coef; a.cacc = s->cacc;

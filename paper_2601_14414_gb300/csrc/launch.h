@@ -32,6 +32,8 @@ struct AdmmLaunch {
   // order-keeping compaction (null: item order, and a compaction that keeps no order)
   const int *list_init;
   int *ccount;
+  int *pos_of;      // [items] position of each item in the active list (null: stopped
+                    // instances leave the list at the next iteration's compaction)
   // fine items (one sub-chunk each) after the nitems coarse ones: nfine of them from index
   // nfine_base; nitems_inst holds the coarse then the fine per-instance counts (0: none)
   int nfine_base, nfine, fine_switch;

@@ -38,6 +38,9 @@ struct Args {
                             // item order), longest first
   int *ccount;              // [grid] per-CTA counts of the order-keeping compaction (null: the
                             // compaction keeps no order)
+  int *pos_of;              // [items] position of each item in the active list: the entries of
+                            // a stopped instance are marked -1 there, and the list is compacted
+                            // once they are a 32nd of it (null: compacted every iteration)
   int nfine_base, nfine;    // fine items: nfine of them from nfine_base (0: none)
   int fine_switch;          // switch to them below fine_switch x grid active coarse items
   int *list[2];
@@ -147,7 +150,7 @@ __device__ inline bool stalled(const Args<T> &a, int j, int it, double c) {
 // Steps 5-7 of instance j given the sum s of its squared step-4 terms (c^{i+1} = rho s): the stop
 // tests, then the momentum decision and factor. Called by one thread.
 template <typename T>
-__device__ inline void apply_steps(const Args<T> &a, int j, int it, double s) {
+__device__ inline bool apply_steps(const Args<T> &a, int j, int it, double s) {
   const double c = a.rho * s;
   InstState &st = a.st[j];
   st.iters = it + 1;
@@ -185,6 +188,7 @@ __device__ inline void apply_steps(const Args<T> &a, int j, int it, double s) {
     atomicSub(&a.ctl->active, 1);
     atomicExch(&a.ctl->stopped, 1);
   }
+  return stop != 0;
 }
 
 // Step 4's reduction is finished by the caller; this adds the item's share of c^{i+1} and, for
@@ -208,8 +212,9 @@ __device__ inline void finish_item(const Args<T> &a, int j, int it, double part)
 // momentum factor) before the next iteration. The items themselves only store their share:
 // no atomics or fences on the item path. Every item of an instance still iterating runs in
 // every iteration (the active list holds all of them), so the shares are complete.
+// An instance that stops has its entries in the active list (cl) marked -1 when pos_of is kept.
 template <typename T>
-__device__ inline bool finish_pass(const Args<T> &a, int it, unsigned nblocks, int *sOk) {
+__device__ inline bool finish_pass(const Args<T> &a, int it, int cl, unsigned nblocks, int *sOk) {
   const int off = *(volatile int *)&a.ctl->fine ? a.L.batch : 0;
   const int stride = (int)nblocks * blockDim.x;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.L.batch; j += stride) {
@@ -217,7 +222,10 @@ __device__ inline bool finish_pass(const Args<T> &a, int it, unsigned nblocks, i
     const int first = a.item_first[j + off], cnt = a.nitems_inst[j + off];
     double s = 0.0;
     for (int i = 0; i < cnt; ++i) s += __ldcg(a.cpart + first + i);
-    apply_steps(a, j, it, s);
+    if (apply_steps(a, j, it, s) && a.pos_of) {
+      for (int i = 0; i < cnt; ++i) a.list[cl][__ldcg(a.pos_of + first + i)] = -1;
+      atomicAdd(&a.ctl->stale, cnt);
+    }
   }
   return grid_sync(a.ctl, nblocks, sOk);
 }
@@ -248,12 +256,17 @@ __device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk, in
   const unsigned nblocks = gridDim.x;
   const bool go_fine =
       a.nfine > 0 && !*(volatile int *)&ctl->fine && nact < a.fine_switch * (int)nblocks;
-  if (!*(volatile int *)&ctl->stopped && !go_fine) return true;
+  const int stopped = *(volatile int *)&ctl->stopped;
+  if (!stopped && !go_fine) return true;
+  if (a.pos_of && !go_fine) {  // marked entries are skipped: compact once they are a 32nd
+    const int stale = *(volatile int *)&ctl->stale;
+    if (stale > 0 && stale * 32 < nact) return true;
+  }
   const int src = cl, dst = cl ^ 1;
   const int total = go_fine ? a.nfine : nact;
   auto entry = [&](int qi, int &item) {  // the qi-th source entry and whether it stays
     item = go_fine ? a.nfine_base + qi : a.list[src][qi];
-    return *(volatile int *)&a.stop[a.item_inst[item]] == 0;
+    return item >= 0 && *(volatile int *)&a.stop[a.item_inst[item]] == 0;
   };
   if (a.ccount) {
     // Order-keeping: CTA b takes a contiguous range of the source list, counts what stays,
@@ -283,12 +296,26 @@ __device__ inline bool compact(const Args<T> &a, int &cl, int nact, int *sOk, in
       __syncthreads();
       int wbase = 0;
       for (int w = 0; w < (tid >> 5); ++w) wbase += red[w];
-      if (keep) a.list[dst][before + wbase + __popc(m & ((1u << (tid & 31)) - 1u))] = item;
+      if (keep) {
+        const int pos = before + wbase + __popc(m & ((1u << (tid & 31)) - 1u));
+        a.list[dst][pos] = item;
+        if (a.pos_of) a.pos_of[item] = pos;
+      }
       int chunk = 0;
       for (int w = 0; w < (nthreads >> 5); ++w) chunk += red[w];
       before += chunk;
     }
-    if (blockIdx.x == 0 && tid == 0) ctl->nlist[dst] = all;
+    // Everyone read nlist[src], stopped and fine before the barrier above; the barrier below
+    // publishes the new list with its length and the reset flags.
+    if (blockIdx.x == 0 && tid == 0) {
+      ctl->nlist[dst] = all;
+      ctl->nlist[src] = 0;
+      ctl->stopped = 0;
+      ctl->stale = 0;
+      if (go_fine) ctl->fine = 1;
+    }
+    cl = dst;
+    return grid_sync(ctl, nblocks, sOk);
   } else {
     for (int b0 = blockIdx.x * nthreads; b0 < total; b0 += nblocks * nthreads) {
       const int qi = b0 + tid;
@@ -332,7 +359,11 @@ __global__ void solve_init_kernel(Args<T> a, int warm) {
     s.iters = 0; s.status = kMaxIter; s.momentum = 0; s.pad = 0; s.c = 0.0;
     a.st[j] = s;
   }
-  if (j < a.nitems) a.list[0][j] = a.list_init ? a.list_init[j] : j;
+  if (j < a.nitems) {
+    const int item = a.list_init ? a.list_init[j] : j;
+    a.list[0][j] = item;
+    if (a.pos_of) a.pos_of[item] = j;
+  }
 }
 
 // Starting iterates: zero (cold start) or the previous solve's iterates shifted one stage.
@@ -409,7 +440,7 @@ Args<T> make_args(const AdmmLaunch &s) {
   a.item_inst = s.item_inst; a.item_a = s.item_a; a.item_b = s.item_b;
   a.nitems = s.nitems; a.nitems_inst = s.nitems_inst;
   a.item_first = s.item_first; a.cpart = s.cpart;
-  a.list_init = s.list_init; a.ccount = s.ccount;
+  a.list_init = s.list_init; a.ccount = s.ccount; a.pos_of = s.pos_of;
   a.nfine_base = s.nfine_base; a.nfine = s.nfine; a.fine_switch = s.fine_switch;
   a.list[0] = s.list0; a.list[1] = s.list1;
   a.ctl = s.ctl;

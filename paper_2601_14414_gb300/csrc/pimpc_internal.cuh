@@ -58,7 +58,8 @@ struct Ctl {
   int nlist[2];          // lengths of the two active-item lists
   int fine;              // the active list holds the fine items (one sub-chunk each)
   int bar_limit;         // polls of the grid barrier before it gives up (0: the default)
-  int pad[5];
+  int stale;             // entries of stopped instances still in the active list (marked -1)
+  int pad[4];
 };
 
 __host__ __device__ inline int packed_size(int n) { return n * (n + 1) / 2; }

@@ -37,6 +37,7 @@ struct pimpc_solver {
   double *cpart = nullptr;    // [items] per-item share of c of the current iteration
   int *list_init = nullptr;   // [coarse items] starting order of the active list
   int *ccount = nullptr;      // [grid] per-CTA counts of the order-keeping compaction
+  int *pos_of = nullptr;      // [items] position of each item in the active list
   pimpc::Ctl *ctl = nullptr;
   int64_t *d_bbase = nullptr;
   pimpc::InstState *st = nullptr;
