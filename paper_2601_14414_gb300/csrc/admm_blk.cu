@@ -14,7 +14,8 @@
 //   * du_k = M_k t_k (M as scalar wrapped diagonals, one lane per input);
 //   * xbar_{k+1} = H_k h_k with H_k stored as wrapped 4 x 4 block diagonals: lane l owns block
 //     row l and, per block diagonal d, applies block (l, l+d) and the transpose of block
-//     (l-d, l), so every lane runs the same code and every read is a 16-byte vector;
+//     (l-d, l), so every lane runs the same code and every read is a 16-byte vector (the middle
+//     diagonal of an even block count is stored once: half the lanes transpose it in registers);
 //   * Abar_k xbar_k and B_k du_k by rows (lane l owns rows l, l+g, ...).
 // A sub-chunk holds S - 1 stages and the next stage, whose group only forms q (the first stage
 // of the next sub-chunk is formed again there). The group left over in the xbar phase of an
@@ -108,13 +109,15 @@ __host__ __device__ inline Regions regions(int nx, int nu, int lti, int tsize, i
 }
 
 // (S h) restricted to the rows 4 I .. 4 I + 3, S symmetric in wrapped 4 x 4 block diagonals at
-// Hb (nb blocks per row, D = nb/2 + 1 block diagonals), h in shared memory (4 nb values).
+// Hb (nb blocks per row; Df full block diagonals, then for an even nb the middle one, stored for
+// block rows below nb/2 only), h in shared memory (4 nb values).
 template <typename T>
-__device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int D, int I) {
+__device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int I) {
   V4<T> acc = zero4<T>();
-  const int rs = D * nb * 4;  // distance between the planes of rows a and a + 1
+  const int Df = bl_full_diags(nb);
+  const int rs = Df * nb * 4;  // distance between the planes of rows a and a + 1
   int Jp = I, Jm = I;
-  for (int d = 0; d < D; ++d) {
+  for (int d = 0; d < Df; ++d) {
     const T *bd = Hb + d * nb * 4;
     {  // block (I, I + d): rows of the block against h_{I+d}
       const V4<T> hv = ld4(h + 4 * Jp);
@@ -125,7 +128,7 @@ __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int
         acc.v[a] += row.v[0] * hv.v[0] + row.v[1] * hv.v[1] + row.v[2] * hv.v[2] + row.v[3] * hv.v[3];
       }
     }
-    if (d > 0 && 2 * d != nb) {  // block (I, I - d) = transpose of block (I - d, I)
+    if (d > 0) {  // block (I, I - d) = transpose of block (I - d, I)
       const V4<T> hm = ld4(h + 4 * Jm);
       const T *bm = bd + Jm * 4;
 #pragma unroll
@@ -137,6 +140,30 @@ __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int
     }
     Jp = (Jp + 1 == nb) ? 0 : Jp + 1;
     Jm = (Jm == 0) ? nb - 1 : Jm - 1;
+  }
+  if (!(nb & 1)) {
+    // The middle diagonal: block (I, I + nb/2) for I < nb/2, else the transpose of block
+    // (I - nb/2, I). Both read the same four rows of the stored block; the transposed case swaps
+    // the loaded rows' off-diagonal entries (selects, no divergent branch).
+    const int hb = nb >> 1;
+    const bool up = I < hb;
+    const int Is = up ? I : I - hb;
+    const V4<T> hv = ld4(h + 4 * (up ? I + hb : Is));
+    const T *bp = Hb + rs * 4 + Is * 4;
+    V4<T> r[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) r[a] = ld4(bp + a * hb * 4);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a + 1; b < 4; ++b) {
+        const T x = r[a].v[b], y = r[b].v[a];
+        r[a].v[b] = up ? x : y;
+        r[b].v[a] = up ? y : x;
+      }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      acc.v[a] += r[a].v[0] * hv.v[0] + r[a].v[1] * hv.v[1] + r[a].v[2] * hv.v[2] + r[a].v[3] * hv.v[3];
   }
   return acc;
 }
@@ -280,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
       // list entries of the instances it stops (-1) until a compaction removes them.
       const int nx = a.L.nx[j], nu = a.L.nu[j], N = a.L.N[j], n = nx + nu;
       const int g = bl_group(n), S = a.grp[j], P = S - 1;
-      const int nP = bl_pad4(n), rec = bl_rec(n), nb = bl_nb(n), D = bl_diags(nb);
+      const int nP = bl_pad4(n), rec = bl_rec(n), nb = bl_nb(n);
       const int ldg = bl_ldg(n, TS), oE = bl_oE(nx, nu, TS), oH = bl_oH(nx, nu, TS);
       const int oM = bl_oM(nx, nu, TS), symW = bl_sym_words(n);
       const int W = a.L.W[j];
@@ -492,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 3) blk_kernel(Args<T> a) {
         if ((stage || hgrp) && l < nb) {
           const T *Hb = stage ? (lti ? ltiB + ((k < N - 1) ? 0 : W) + oH : rB + grp * W + oH)
                               : (lti ? ltiB + oH : hB);
-          const V4<T> x = sym_blocks(Hb, sY, nb, D, l);
+          const V4<T> x = sym_blocks(Hb, sY, nb, l);
           if (stage) {
             st4(Xc + (grp + 1) * nP + c0, x);
             if (grp + 1 == cnt) st4(Xn + c0, x);  // row 0 of the next sub-chunk

@@ -172,10 +172,17 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   // as wrapped 4 x 4 block diagonals (slot w is element (a, b) of block (d, I), see
   // bl_sym_index).
   auto put_sym_blocks = [&](int o, int m, const double *Xs, int ldx) {
-    const int nbm = bl_nb(m), Dm = bl_diags(nbm);
-    for (int w = lane; w < 16 * nbm * Dm; w += 32) {
-      const int b = w & 3, q = w >> 2;
-      const int I = q % nbm, d = (q / nbm) % Dm, a4 = q / (nbm * Dm);
+    const int nbm = bl_nb(m), Df = bl_full_diags(nbm), full = 16 * nbm * Df;
+    for (int w = lane; w < bl_sym_words(m); w += 32) {
+      int I, d, a4;
+      const int b = w & 3;
+      if (w < full) {
+        const int q = w >> 2;
+        I = q % nbm; d = (q / nbm) % Df; a4 = q / (nbm * Df);
+      } else {  // the middle block diagonal of an even nb, block rows I < nb/2
+        const int q = (w - full) >> 2, hb = nbm >> 1;
+        I = q % hb; d = hb; a4 = q / hb;
+      }
       const int r = 4 * I + a4, c = 4 * ((I + d) % nbm) + b;
       put(o + w, (r < m && c < m) ? Xs[r * ldx + c] : 0.0);
     }

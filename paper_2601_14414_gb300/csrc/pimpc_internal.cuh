@@ -116,10 +116,13 @@ __host__ __device__ inline int halo_copies(int tw, int N, int k, int *tt, int *s
 //   [ G_k : nx rows of stride bl_ldg(n) ][ e_k : nx, padded to 4 ][ H_k as wrapped 4 x 4 block
 //   diagonals ][ M_k as (scalar) wrapped diagonals, padded to 4 ]
 // H_k (n x n, zero-padded to 4 nb, nb = ceil(n / 4)) is cut into 4 x 4 blocks S_{I,J}; for
-// d = 0 .. nb/2 the block S_{I,(I+d) mod nb} is stored for every block row I (blocks d and
-// nb - d are transposes of each other, so this holds every block once, those with d = nb/2 of an
-// even nb twice). Row a of block (d, I) sits at ((a D + d) nb + I) * 4 (D = nb/2 + 1): lanes
-// reading row a of consecutive blocks read consecutive 16-byte words. The G stride is chosen for
+// d = 0 .. nb/2 the block S_{I,(I+d) mod nb} is stored (blocks d and nb - d are transposes of
+// each other, so this holds every block once). The full block diagonals d < Df = ceil(nb / 2)
+// hold a block for every block row I: row a of block (d, I) sits at ((a Df + d) nb + I) * 4, so
+// lanes reading row a of consecutive blocks read consecutive 16-byte words. For an even nb the
+// middle diagonal d = nb/2 pairs block rows I and I + nb/2 (S_{I+nb/2,I} is the transpose of
+// S_{I,I+nb/2}), so it is stored for I < nb/2 only, after the full ones: row a of its block I at
+// 16 nb Df + (a nb/2 + I) * 4. The G stride is chosen for
 // the row products, where lane l of a group reads row l: FP32 rows are 4 nb words long when nb
 // is odd (an odd number of 16-byte words: rows l = 0..7 start in distinct 16-byte bank groups)
 // or 4 or 8 (lane l then reads, at step J, block (J + l) mod nb of its row, which again puts
@@ -137,12 +140,21 @@ __host__ __device__ inline int bl_ldg(int n, int tsize) {
   if (tsize != 4) return 4 * nb + 2;
   return ((nb & 1) || nb <= 2 || bl_rot(nb)) ? 4 * nb : 4 * (nb + 1);
 }
+// Full block diagonals (a block for every block row); an even nb adds the half-stored middle one.
+__host__ __device__ inline int bl_full_diags(int nb) { return (nb + 1) >> 1; }
 __host__ __device__ inline int bl_sym_words(int m) {
   const int nb = bl_nb(m);
-  return 16 * nb * bl_diags(nb);
+  return 16 * nb * bl_full_diags(nb) + ((nb & 1) ? 0 : 8 * nb);
+}
+// Whether block (d, I) has a slot of its own (d <= nb/2; the middle diagonal of an even nb only
+// for I < nb/2).
+__host__ __device__ inline bool bl_sym_stored(int nb, int d, int I) {
+  return d < bl_full_diags(nb) || I < (nb >> 1);
 }
 __host__ __device__ inline int bl_sym_index(int nb, int d, int I, int a, int b) {
-  return ((a * bl_diags(nb) + d) * nb + I) * 4 + b;
+  const int Df = bl_full_diags(nb);
+  if (d < Df) return ((a * Df + d) * nb + I) * 4 + b;
+  return 16 * nb * Df + (a * (nb >> 1) + I) * 4 + b;
 }
 // Offsets inside a blocked stage block: e, H, M; and the block size W.
 __host__ __device__ inline int bl_oE(int nx, int nu, int tsize) { return nx * bl_ldg(nx + nu, tsize); }

@@ -5,11 +5,13 @@ here with g++ includes that header and prints, for every matrix size m = 1..64, 
 the number of stored block diagonals, the storage size and the storage index of every (block
 diagonal d, block row I, row a, column b) slot, plus the G strides and block offsets. The test
 then checks what the solve kernel relies on:
-  * the storage index is a bijection onto [0, bl_sym_words(m));
-  * storing S_{I,(I+d) mod nb} for d <= nb/2 holds every element of a symmetric m x m matrix;
-  * the per-lane product the kernel runs (per block diagonal: block (I, I+d) against h_{I+d},
-    the transpose of block (I-d, I) against h_{I-d}, the middle diagonal of an even nb once)
-    reproduces S h;
+  * the storage index is a bijection onto [0, bl_sym_words(m)), and the slots are exactly the
+    blocks S_{I,(I+d) mod nb} for d < nb/2 and, for d = nb/2, the block rows I below nb/2 of an
+    even nb (every 4 x 4 block of a symmetric matrix once, up to transposition);
+  * storing those blocks holds every element of a symmetric m x m matrix;
+  * the per-lane product the kernel runs (per full block diagonal: block (I, I+d) against
+    h_{I+d}, the transpose of block (I-d, I) against h_{I-d}; the middle diagonal of an even nb:
+    block (I, I+nb/2) for I < nb/2, else the transpose of block (I-nb/2, I)) reproduces S h;
   * G rows start 16-byte aligned; the FP32 row products (lane l reads row l, in a rotated block
     order for block counts 4 and 8) and 8 consecutive FP64 rows hit distinct 16-byte bank
     groups; every offset inside a block is 16-byte aligned.
@@ -35,6 +37,7 @@ int main() {
     std::printf("M %d %d %d %d %d %d\n", m, nb, D, bl_sym_words(m), bl_ldg(m, 4), bl_ldg(m, 8));
     for (int d = 0; d < D; ++d)
       for (int I = 0; I < nb; ++I)
+        if (bl_sym_stored(nb, d, I))
         for (int a = 0; a < 4; ++a)
           for (int b = 0; b < 4; ++b) std::printf("S %d %d %d %d %d\n", d, I, a, b, bl_sym_index(nb, d, I, a, b));
   }
@@ -78,9 +81,16 @@ def layout(tmp_path_factory):
 def test_storage_index_is_a_bijection(layout):
     mats, _ = layout
     for m, L in mats.items():
-        assert L["nb"] == (m + 3) // 4 and L["D"] == L["nb"] // 2 + 1
+        nb = L["nb"]
+        assert nb == (m + 3) // 4 and L["D"] == nb // 2 + 1
         vals = sorted(L["idx"].values())
         assert vals == list(range(L["words"])), m
+        slots = {(d, I) for (d, I, a, b) in L["idx"]}
+        want = {(d, I) for d in range(nb // 2 + 1) for I in range(nb)
+                if 2 * d < nb or (2 * d == nb and I < nb // 2) or nb == 1}
+        assert slots == want, m
+        # one slot per block of the upper block triangle (I <= J) of the padded matrix
+        assert len(slots) == nb * (nb + 1) // 2, m
 
 
 def stored(L, S):
@@ -107,22 +117,29 @@ def test_every_element_is_held_and_the_lane_products_give_S_h(layout):
             for c in range(m):
                 I, a, J, b = r // 4, r % 4, c // 4, c % 4
                 d = (J - I) % nb
-                if 2 * d > nb:
-                    d, I, J, a, b = nb - d, J, I, b, a
+                if 2 * d > nb or (2 * d == nb and I >= nb // 2 and nb > 1):
+                    d, I, J, a, b = (nb - d) % nb, J, I, b, a
                 assert H[idx[(d, I, a, b)]] == S[r, c]
         # the lane products of the solve kernel
         h = np.zeros(4 * nb)
         h[:m] = rng.standard_normal(m)
         y = np.zeros(4 * nb)
+        def block(d, I):
+            return np.array([[H[idx[(d, I, a, b)]] for b in range(4)] for a in range(4)])
+        Df = (nb + 1) // 2
         for I in range(nb):
-            for d in range(D):
+            for d in range(Df):
                 Jp = (I + d) % nb
-                blk = np.array([[H[idx[(d, I, a, b)]] for b in range(4)] for a in range(4)])
-                y[4 * I:4 * I + 4] += blk @ h[4 * Jp:4 * Jp + 4]
-                if d > 0 and 2 * d != nb:
+                y[4 * I:4 * I + 4] += block(d, I) @ h[4 * Jp:4 * Jp + 4]
+                if d > 0:
                     Jm = (I - d) % nb
-                    bt = np.array([[H[idx[(d, Jm, a, b)]] for b in range(4)] for a in range(4)])
-                    y[4 * I:4 * I + 4] += bt.T @ h[4 * Jm:4 * Jm + 4]
+                    y[4 * I:4 * I + 4] += block(d, Jm).T @ h[4 * Jm:4 * Jm + 4]
+            if nb % 2 == 0:
+                hb = nb // 2
+                if I < hb:
+                    y[4 * I:4 * I + 4] += block(hb, I) @ h[4 * (I + hb):4 * (I + hb) + 4]
+                else:
+                    y[4 * I:4 * I + 4] += block(hb, I - hb).T @ h[4 * (I - hb):4 * (I - hb) + 4]
         np.testing.assert_allclose(y[:m], S @ h[:m], rtol=1e-12, atol=1e-12)
         assert np.all(y[m:] == 0)
 
