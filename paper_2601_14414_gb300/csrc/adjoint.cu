@@ -117,17 +117,17 @@ __device__ __forceinline__ T sym_at(const T *Wp, int m, int r, int c) {
 
 // Element (r, c) of a symmetric m x m matrix stored as wrapped 4 x 4 block diagonals (block
 // (d, I) = S_{I, (I+d) mod nb} for d <= nb / 2; the middle diagonal of an even nb only for
-// I < nb / 2).
+// I < nb / 2; the diagonal blocks d = 0 only their upper triangles).
 template <typename T>
 __device__ __forceinline__ T sym_block_at(const T *Hb, int m, int r, int c) {
   const int nb = bl_nb(m);
   int I = r >> 2, a = r & 3, J = c >> 2, b = c & 3;
   int d = J - I;
   if (d < 0) d += nb;
-  if (2 * d > nb || (2 * d == nb && I >= (nb >> 1))) {
+  if (2 * d > nb || (2 * d == nb && I >= (nb >> 1)) || (d == 0 && a > b)) {
     // stored as the transpose: block (nb - d, J) (the middle diagonal of an even nb: block row
-    // J = I - nb/2), element (b, a)
-    d = nb - d;
+    // J = I - nb/2; a diagonal block: its upper triangle), element (b, a)
+    d = d == 0 ? 0 : nb - d;
     int t = I; I = J; J = t;
     t = a; a = b; b = t;
   }

@@ -14,7 +14,8 @@
 //   * du_k = M_k t_k (M as scalar wrapped diagonals, one lane per input);
 //   * xbar_{k+1} = H_k h_k with H_k stored as wrapped 4 x 4 block diagonals: lane l owns block
 //     row l and, per block diagonal d, applies block (l, l+d) and the transpose of block
-//     (l-d, l), so every lane runs the same code and every read is a 16-byte vector (the middle
+//     (l-d, l), so every lane runs the same code and every read is a 16-byte vector (the
+//     symmetric diagonal blocks are stored as upper triangles, read as 8-byte pairs; the middle
 //     diagonal of an even block count is stored once: half the lanes transpose it in registers);
 //   * Abar_k xbar_k and B_k du_k by rows (lane l owns rows l, l+g, ...).
 // A sub-chunk holds S - 1 stages and the next stage, whose group only forms q (the first stage
@@ -81,6 +82,17 @@ __device__ __forceinline__ V4<double> ldg4(const double *p) {
   const double2 q1 = __ldcg(reinterpret_cast<const double2 *>(p + 2));
   return {{q0.x, q0.y, q1.x, q1.y}};
 }
+// Two consecutive values at an 8-byte (FP32) or 16-byte (FP64) aligned address.
+__device__ __forceinline__ void ld2(const float *p, float &x, float &y) {
+  const float2 q = *reinterpret_cast<const float2 *>(p);
+  x = q.x;
+  y = q.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double &x, double &y) {
+  const double2 q = *reinterpret_cast<const double2 *>(p);
+  x = q.x;
+  y = q.y;
+}
 template <typename T>
 __device__ __forceinline__ V4<T> zero4() {
   return {{(T)0, (T)0, (T)0, (T)0}};
@@ -109,16 +121,31 @@ __host__ __device__ inline Regions regions(int nx, int nu, int lti, int tsize, i
 }
 
 // (S h) restricted to the rows 4 I .. 4 I + 3, S symmetric in wrapped 4 x 4 block diagonals at
-// Hb (nb blocks per row; Df full block diagonals, then for an even nb the middle one, stored for
-// block rows below nb/2 only), h in shared memory (4 nb values).
+// Hb (nb blocks per row: the diagonal blocks' upper triangles, Df - 1 further full block
+// diagonals, then for an even nb the middle one, stored for block rows below nb/2 only), h in
+// shared memory (4 nb values).
 template <typename T>
 __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int I) {
-  V4<T> acc = zero4<T>();
+  V4<T> acc;
+  {  // block (I, I) from its upper triangle (five aligned pairs)
+    const T *p = Hb + 10 * I;
+    T s[10];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) ld2(p + 2 * q, s[2 * q], s[2 * q + 1]);
+    const V4<T> hv = ld4(h + 4 * I);
+    acc.v[0] = s[0] * hv.v[0] + s[1] * hv.v[1] + s[2] * hv.v[2] + s[3] * hv.v[3];
+    acc.v[1] = s[1] * hv.v[0] + s[4] * hv.v[1] + s[5] * hv.v[2] + s[6] * hv.v[3];
+    acc.v[2] = s[2] * hv.v[0] + s[5] * hv.v[1] + s[7] * hv.v[2] + s[8] * hv.v[3];
+    acc.v[3] = s[3] * hv.v[0] + s[6] * hv.v[1] + s[8] * hv.v[2] + s[9] * hv.v[3];
+  }
   const int Df = bl_full_diags(nb);
-  const int rs = Df * nb * 4;  // distance between the planes of rows a and a + 1
+  const T *Hf = Hb + bl_diag_words(nb);
+  const int rs = (Df - 1) * nb * 4;  // distance between the planes of rows a and a + 1
   int Jp = I, Jm = I;
-  for (int d = 0; d < Df; ++d) {
-    const T *bd = Hb + d * nb * 4;
+  for (int d = 1; d < Df; ++d) {
+    Jp = (Jp + 1 == nb) ? 0 : Jp + 1;
+    Jm = (Jm == 0) ? nb - 1 : Jm - 1;
+    const T *bd = Hf + (d - 1) * nb * 4;
     {  // block (I, I + d): rows of the block against h_{I+d}
       const V4<T> hv = ld4(h + 4 * Jp);
       const T *bp = bd + I * 4;
@@ -128,7 +155,7 @@ __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int
         acc.v[a] += row.v[0] * hv.v[0] + row.v[1] * hv.v[1] + row.v[2] * hv.v[2] + row.v[3] * hv.v[3];
       }
     }
-    if (d > 0) {  // block (I, I - d) = transpose of block (I - d, I)
+    {  // block (I, I - d) = transpose of block (I - d, I)
       const V4<T> hm = ld4(h + 4 * Jm);
       const T *bm = bd + Jm * 4;
 #pragma unroll
@@ -138,8 +165,6 @@ __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int
         for (int b = 0; b < 4; ++b) acc.v[b] += row.v[b] * hm.v[a];
       }
     }
-    Jp = (Jp + 1 == nb) ? 0 : Jp + 1;
-    Jm = (Jm == 0) ? nb - 1 : Jm - 1;
   }
   if (!(nb & 1)) {
     // The middle diagonal: block (I, I + nb/2) for I < nb/2, else the transpose of block
@@ -149,7 +174,7 @@ __device__ __forceinline__ V4<T> sym_blocks(const T *Hb, const T *h, int nb, int
     const bool up = I < hb;
     const int Is = up ? I : I - hb;
     const V4<T> hv = ld4(h + 4 * (up ? I + hb : Is));
-    const T *bp = Hb + rs * 4 + Is * 4;
+    const T *bp = Hf + rs * 4 + Is * 4;
     V4<T> r[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) r[a] = ld4(bp + a * hb * 4);

@@ -117,12 +117,15 @@ __host__ __device__ inline int halo_copies(int tw, int N, int k, int *tt, int *s
 //   diagonals ][ M_k as (scalar) wrapped diagonals, padded to 4 ]
 // H_k (n x n, zero-padded to 4 nb, nb = ceil(n / 4)) is cut into 4 x 4 blocks S_{I,J}; for
 // d = 0 .. nb/2 the block S_{I,(I+d) mod nb} is stored (blocks d and nb - d are transposes of
-// each other, so this holds every block once). The full block diagonals d < Df = ceil(nb / 2)
-// hold a block for every block row I: row a of block (d, I) sits at ((a Df + d) nb + I) * 4, so
+// each other, so this holds every block once). The diagonal blocks (d = 0) are symmetric: block
+// I keeps its upper triangle, row by row (s00 s01 s02 s03 s11 s12 s13 s22 s23 s33), at 10 I,
+// so a lane reads it as five 8-byte pairs (the region padded to 4 words). The other full block
+// diagonals 1 <= d < Df = ceil(nb / 2) hold a block for every block row I: row a of block
+// (d, I) sits at D0 + ((a (Df - 1) + d - 1) nb + I) * 4 (D0 = the padded diagonal region), so
 // lanes reading row a of consecutive blocks read consecutive 16-byte words. For an even nb the
 // middle diagonal d = nb/2 pairs block rows I and I + nb/2 (S_{I+nb/2,I} is the transpose of
-// S_{I,I+nb/2}), so it is stored for I < nb/2 only, after the full ones: row a of its block I at
-// 16 nb Df + (a nb/2 + I) * 4. The G stride is chosen for
+// S_{I,I+nb/2}), so it is stored for I < nb/2 only, after the full ones: row a of its block I
+// at D0 + 16 nb (Df - 1) + (a nb/2 + I) * 4. The G stride is chosen for
 // the row products, where lane l of a group reads row l: FP32 rows are 4 nb words long when nb
 // is odd (an odd number of 16-byte words: rows l = 0..7 start in distinct 16-byte bank groups)
 // or 4 or 8 (lane l then reads, at step J, block (J + l) mod nb of its row, which again puts
@@ -140,21 +143,28 @@ __host__ __device__ inline int bl_ldg(int n, int tsize) {
   if (tsize != 4) return 4 * nb + 2;
   return ((nb & 1) || nb <= 2 || bl_rot(nb)) ? 4 * nb : 4 * (nb + 1);
 }
-// Full block diagonals (a block for every block row); an even nb adds the half-stored middle one.
+// Block diagonals with a block for every block row (d = 0 included); an even nb adds the
+// half-stored middle one.
 __host__ __device__ inline int bl_full_diags(int nb) { return (nb + 1) >> 1; }
+// Words of the diagonal blocks' upper triangles (10 per block, padded to 4).
+__host__ __device__ inline int bl_diag_words(int nb) { return (10 * nb + 3) & ~3; }
+// Slot of element (a, b), a <= b, in a diagonal block's upper triangle.
+__host__ __device__ inline int bl_tri(int a, int b) { return a * 4 - ((a * (a - 1)) >> 1) + b - a; }
 __host__ __device__ inline int bl_sym_words(int m) {
   const int nb = bl_nb(m);
-  return 16 * nb * bl_full_diags(nb) + ((nb & 1) ? 0 : 8 * nb);
+  return bl_diag_words(nb) + 16 * nb * (bl_full_diags(nb) - 1) + ((nb & 1) ? 0 : 8 * nb);
 }
-// Whether block (d, I) has a slot of its own (d <= nb/2; the middle diagonal of an even nb only
-// for I < nb/2).
-__host__ __device__ inline bool bl_sym_stored(int nb, int d, int I) {
+// Whether element (a, b) of block (d, I) has a slot of its own (d <= nb/2; the middle diagonal
+// of an even nb only for I < nb/2; a diagonal block only its upper triangle, a <= b).
+__host__ __device__ inline bool bl_sym_stored(int nb, int d, int I, int a, int b) {
+  if (d == 0) return a <= b;
   return d < bl_full_diags(nb) || I < (nb >> 1);
 }
 __host__ __device__ inline int bl_sym_index(int nb, int d, int I, int a, int b) {
-  const int Df = bl_full_diags(nb);
-  if (d < Df) return ((a * Df + d) * nb + I) * 4 + b;
-  return 16 * nb * Df + (a * (nb >> 1) + I) * 4 + b;
+  if (d == 0) return 10 * I + bl_tri(a, b);
+  const int Df = bl_full_diags(nb), D0 = bl_diag_words(nb);
+  if (d < Df) return D0 + ((a * (Df - 1) + d - 1) * nb + I) * 4 + b;
+  return D0 + 16 * nb * (Df - 1) + (a * (nb >> 1) + I) * 4 + b;
 }
 // Offsets inside a blocked stage block: e, H, M; and the block size W.
 __host__ __device__ inline int bl_oE(int nx, int nu, int tsize) { return nx * bl_ldg(nx + nu, tsize); }

@@ -5,13 +5,16 @@ here with g++ includes that header and prints, for every matrix size m = 1..64, 
 the number of stored block diagonals, the storage size and the storage index of every (block
 diagonal d, block row I, row a, column b) slot, plus the G strides and block offsets. The test
 then checks what the solve kernel relies on:
-  * the storage index is a bijection onto [0, bl_sym_words(m)), and the slots are exactly the
-    blocks S_{I,(I+d) mod nb} for d < nb/2 and, for d = nb/2, the block rows I below nb/2 of an
-    even nb (every 4 x 4 block of a symmetric matrix once, up to transposition);
+  * the storage index is injective into [0, bl_sym_words(m)) and leaves only the padding of the
+    diagonal-block region unused; the slots are exactly the upper triangles of the diagonal
+    blocks, the blocks S_{I,(I+d) mod nb} for 0 < d < nb/2 and, for d = nb/2, the block rows I
+    below nb/2 of an even nb (every element of a symmetric matrix once, up to symmetry); the
+    diagonal blocks' pairs and every other block row are aligned for the kernel's vector reads;
   * storing those blocks holds every element of a symmetric m x m matrix;
-  * the per-lane product the kernel runs (per full block diagonal: block (I, I+d) against
-    h_{I+d}, the transpose of block (I-d, I) against h_{I-d}; the middle diagonal of an even nb:
-    block (I, I+nb/2) for I < nb/2, else the transpose of block (I-nb/2, I)) reproduces S h;
+  * the per-lane product the kernel runs (the diagonal block rebuilt from its upper triangle;
+    per further full block diagonal: block (I, I+d) against h_{I+d}, the transpose of block
+    (I-d, I) against h_{I-d}; the middle diagonal of an even nb: block (I, I+nb/2) for
+    I < nb/2, else the transpose of block (I-nb/2, I)) reproduces S h;
   * G rows start 16-byte aligned; the FP32 row products (lane l reads row l, in a rotated block
     order for block counts 4 and 8) and 8 consecutive FP64 rows hit distinct 16-byte bank
     groups; every offset inside a block is 16-byte aligned.
@@ -37,9 +40,10 @@ int main() {
     std::printf("M %d %d %d %d %d %d\n", m, nb, D, bl_sym_words(m), bl_ldg(m, 4), bl_ldg(m, 8));
     for (int d = 0; d < D; ++d)
       for (int I = 0; I < nb; ++I)
-        if (bl_sym_stored(nb, d, I))
         for (int a = 0; a < 4; ++a)
-          for (int b = 0; b < 4; ++b) std::printf("S %d %d %d %d %d\n", d, I, a, b, bl_sym_index(nb, d, I, a, b));
+          for (int b = 0; b < 4; ++b)
+            if (bl_sym_stored(nb, d, I, a, b))
+              std::printf("S %d %d %d %d %d\n", d, I, a, b, bl_sym_index(nb, d, I, a, b));
   }
   for (int nx = 1; nx <= 40; ++nx)
     for (int nu = 1; nu <= 24; ++nu)
@@ -84,13 +88,26 @@ def test_storage_index_is_a_bijection(layout):
         nb = L["nb"]
         assert nb == (m + 3) // 4 and L["D"] == nb // 2 + 1
         vals = sorted(L["idx"].values())
-        assert vals == list(range(L["words"])), m
+        assert len(set(vals)) == len(vals), m
+        d0w = (10 * nb + 3) // 4 * 4
+        unused = set(range(L["words"])) - set(vals)
+        assert unused == set(range(10 * nb, d0w)), m  # only the diagonal region's padding
         slots = {(d, I) for (d, I, a, b) in L["idx"]}
         want = {(d, I) for d in range(nb // 2 + 1) for I in range(nb)
                 if 2 * d < nb or (2 * d == nb and I < nb // 2) or nb == 1}
         assert slots == want, m
         # one slot per block of the upper block triangle (I <= J) of the padded matrix
         assert len(slots) == nb * (nb + 1) // 2, m
+        # the diagonal blocks hold exactly their upper triangles, at 10 I, read as aligned pairs
+        for I in range(nb):
+            tri = sorted(k for (d, J, a, b), k in L["idx"].items() if d == 0 and J == I)
+            assert tri == list(range(10 * I, 10 * I + 10)), (m, I)
+            assert {(a, b) for (d, J, a, b) in L["idx"] if d == 0 and J == I} == \
+                {(a, b) for a in range(4) for b in range(a, 4)}, (m, I)
+        # rows of the other blocks start 16-byte aligned (FP32 words) and run over 4 slots
+        for (d, I, a, b), k in L["idx"].items():
+            if d > 0:
+                assert (k - b) % 4 == 0 and L["idx"][(d, I, a, 0)] + b == k, (m, d, I, a, b)
 
 
 def stored(L, S):
@@ -117,7 +134,7 @@ def test_every_element_is_held_and_the_lane_products_give_S_h(layout):
             for c in range(m):
                 I, a, J, b = r // 4, r % 4, c // 4, c % 4
                 d = (J - I) % nb
-                if 2 * d > nb or (2 * d == nb and I >= nb // 2 and nb > 1):
+                if 2 * d > nb or (2 * d == nb and I >= nb // 2 and nb > 1) or (d == 0 and a > b):
                     d, I, J, a, b = (nb - d) % nb, J, I, b, a
                 assert H[idx[(d, I, a, b)]] == S[r, c]
         # the lane products of the solve kernel
@@ -126,14 +143,19 @@ def test_every_element_is_held_and_the_lane_products_give_S_h(layout):
         y = np.zeros(4 * nb)
         def block(d, I):
             return np.array([[H[idx[(d, I, a, b)]] for b in range(4)] for a in range(4)])
+
+        def diag_block(I):
+            t = [H[10 * I + q] for q in range(10)]  # s00 s01 s02 s03 s11 s12 s13 s22 s23 s33
+            return np.array([[t[0], t[1], t[2], t[3]], [t[1], t[4], t[5], t[6]],
+                             [t[2], t[5], t[7], t[8]], [t[3], t[6], t[8], t[9]]])
         Df = (nb + 1) // 2
         for I in range(nb):
-            for d in range(Df):
+            y[4 * I:4 * I + 4] += diag_block(I) @ h[4 * I:4 * I + 4]
+            for d in range(1, Df):
                 Jp = (I + d) % nb
                 y[4 * I:4 * I + 4] += block(d, I) @ h[4 * Jp:4 * Jp + 4]
-                if d > 0:
-                    Jm = (I - d) % nb
-                    y[4 * I:4 * I + 4] += block(d, Jm).T @ h[4 * Jm:4 * Jm + 4]
+                Jm = (I - d) % nb
+                y[4 * I:4 * I + 4] += block(d, Jm).T @ h[4 * Jm:4 * Jm + 4]
             if nb % 2 == 0:
                 hb = nb // 2
                 if I < hb:
