@@ -128,29 +128,59 @@ __device__ inline bool grid_sync(Ctl *c, unsigned nblocks, int *sOk) {
   return *sOk != 0;
 }
 
+// Per-instance state that steps 5-7 read. It does not depend on c^{i+1}, so the pass over the
+// instances loads it in the same round as the item counts, before the shares of c arrive.
+struct StepState {
+  double cprev, alpha, cbest;
+  int momentum, itfirst, itbest;
+};
+
+template <typename T>
+__device__ inline StepState load_step_state(const Args<T> &a, int j) {
+  StepState q;
+  q.cprev = a.cprev[j];
+  q.alpha = a.alpha[j];
+  q.momentum = a.st[j].momentum;
+  if (a.stall_win > 0) {
+    q.cbest = a.cbest[j];
+    q.itfirst = a.itfirst[j];
+    q.itbest = a.itbest[j];
+  } else {
+    q.cbest = 0.0;
+    q.itfirst = q.itbest = 0;
+  }
+  return q;
+}
+
 // The floor of the iteration's arithmetic: since c^{i+1} first came below stall_below (at
 // iteration i0), it has not fallen below stall_fac times the best c for max(stall_win,
 // stall_rel i0) iterations. In FP32 c stops decreasing once the rounding of the iterates
 // dominates their change; plateaus of the accelerated iteration far above that floor do not
 // count, and the window grows with i0 because an instance that converges slowly (large i0)
 // keeps improving its iterates for longer after its c has levelled off. Updates the best c.
-// Called by one thread, only for c <= stall_below.
+// Called by one thread, only for c <= stall_below; q holds the instance's state as loaded.
 template <typename T>
-__device__ inline bool stalled(const Args<T> &a, int j, int it, double c) {
-  if (a.itfirst[j] < 0) a.itfirst[j] = it;
-  if (c < a.stall_fac * a.cbest[j]) {
+__device__ inline bool stalled(const Args<T> &a, int j, int it, double c, StepState &q) {
+  if (q.itfirst < 0) {
+    q.itfirst = it;
+    a.itfirst[j] = it;
+  }
+  if (c < a.stall_fac * q.cbest) {
+    q.cbest = c;
+    q.itbest = it;
     a.cbest[j] = c;
     a.itbest[j] = it;
     return false;
   }
-  const double win = fmax((double)a.stall_win, a.stall_rel * (double)a.itfirst[j]);
-  return (double)(it - a.itbest[j]) >= win;
+  const double win = fmax((double)a.stall_win, a.stall_rel * (double)q.itfirst);
+  return (double)(it - q.itbest) >= win;
 }
 
 // Steps 5-7 of instance j given the sum s of its squared step-4 terms (c^{i+1} = rho s): the stop
-// tests, then the momentum decision and factor. Called by one thread.
+// tests, then the momentum decision and factor. Called by one thread; q is the instance's state
+// (load_step_state), written back where it changes.
 template <typename T>
-__device__ inline bool apply_steps(const Args<T> &a, int j, int it, double s) {
+__device__ inline bool apply_steps(const Args<T> &a, int j, int it, double s, StepState q) {
   const double c = a.rho * s;
   InstState &st = a.st[j];
   st.iters = it + 1;
@@ -160,7 +190,7 @@ __device__ inline bool apply_steps(const Args<T> &a, int j, int it, double s) {
     st.status = kNonFinite; stop = 1;
   } else if (c <= a.eps) {
     st.status = kConverged; stop = 1;
-  } else if (a.stall_win > 0 && c <= a.stall_below && stalled(a, j, it, c)) {
+  } else if (a.stall_win > 0 && c <= a.stall_below && stalled(a, j, it, c, q)) {
     st.status = kStalled; stop = 1;
   } else if (it + 1 >= a.max_iters) {
     st.status = kMaxIter; stop = 1;
@@ -168,14 +198,14 @@ __device__ inline bool apply_steps(const Args<T> &a, int j, int it, double s) {
     int take = 0;
     if (a.accel) {
       if (a.mask && it < a.mask_len) take = a.mask[(int64_t)j * a.mask_len + it] != 0;
-      else take = c <= a.eta * a.cprev[j];
+      else take = c <= a.eta * q.cprev;
     }
     if (take) {
-      const double al = a.alpha[j];
+      const double al = q.alpha;
       const double an = 0.5 + 0.5 * sqrt(1.0 + 4.0 * al * al);
       a.coef[j] = (al - 1.0) / an;
       a.alpha[j] = an;
-      if (al != 1.0) st.momentum += 1;
+      if (al != 1.0) st.momentum = q.momentum + 1;
     } else {
       a.alpha[j] = 1.0;
       a.coef[j] = 0.0;
@@ -203,7 +233,7 @@ __device__ inline void finish_item(const Args<T> &a, int j, int it, double part)
   __threadfence();
   const double s = __longlong_as_double((long long)atomicExch((unsigned long long *)&a.cacc[j], 0ull));
   a.ndone[j] = 0;
-  apply_steps(a, j, it, s);
+  apply_steps(a, j, it, s, load_step_state(a, j));
 }
 
 // After the iteration's grid barrier: steps 5-7 for every instance still iterating, from the
@@ -213,16 +243,24 @@ __device__ inline void finish_item(const Args<T> &a, int j, int it, double part)
 // no atomics or fences on the item path. Every item of an instance still iterating runs in
 // every iteration (the active list holds all of them), so the shares are complete.
 // An instance that stops has its entries in the active list (cl) marked -1 when pos_of is kept.
+// The loads that do not depend on each other (the stop flag, both item ranges, the state of
+// steps 5-7) are issued together, so that the pass waits on two rounds of loads: those and the
+// shares of c.
 template <typename T>
 __device__ inline bool finish_pass(const Args<T> &a, int it, int cl, unsigned nblocks, int *sOk) {
-  const int off = *(volatile int *)&a.ctl->fine ? a.L.batch : 0;
+  const int fine = *(volatile int *)&a.ctl->fine;
   const int stride = (int)nblocks * blockDim.x;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.L.batch; j += stride) {
-    if (*(volatile int *)&a.stop[j]) continue;
-    const int first = a.item_first[j + off], cnt = a.nitems_inst[j + off];
+  const int B = a.L.batch;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B; j += stride) {
+    const int stopped = *(volatile int *)&a.stop[j];
+    const int f0 = a.item_first[j], n0 = a.nitems_inst[j];
+    const int f1 = a.item_first[j + B], n1 = a.nitems_inst[j + B];
+    const StepState q = load_step_state(a, j);
+    if (stopped) continue;
+    const int first = fine ? f1 : f0, cnt = fine ? n1 : n0;
     double s = 0.0;
     for (int i = 0; i < cnt; ++i) s += __ldcg(a.cpart + first + i);
-    if (apply_steps(a, j, it, s) && a.pos_of) {
+    if (apply_steps(a, j, it, s, q) && a.pos_of) {
       for (int i = 0; i < cnt; ++i) a.list[cl][__ldcg(a.pos_of + first + i)] = -1;
       atomicAdd(&a.ctl->stale, cnt);
     }
