@@ -44,8 +44,13 @@ __host__ __device__ inline int res_stride(int n, int tsize) {
   return (5 * n + q - 1) / q * q;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) resident_kernel(Args<T> a, ResPlan pl) {
+// kMinCtas: the CTAs of 256 threads per SM that the registers are capped for (0: no cap beyond
+// the block size, the default). A batch of many small instances (more CTAs than the SMs hold at
+// once) runs the variant capped for 4 in FP32 (64 registers, no spills): fewer waves. A cluster
+// that spans one instance keeps the default, whose larger register budget shortens each
+// iteration's critical path.
+template <typename T, int kMinCtas>
+__global__ void __launch_bounds__(256, kMinCtas) resident_kernel(Args<T> a, ResPlan pl) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double sPart;
   __shared__ double sRed[8];
@@ -332,7 +337,13 @@ cudaError_t launch_t(const AdmmLaunch &s, const ResPlan &pl, size_t smem, cudaSt
     if ((rc = cudaGetLastError()) != cudaSuccess) return rc;
   }
   if (s.max_iters > 0) {
-    const void *kernel = (const void *)resident_kernel<T>;
+    const void *kernel = (const void *)resident_kernel<T, 0>;
+    if constexpr (sizeof(T) == 4) {
+      int dev = 0, nsm = 0;
+      if ((rc = cudaGetDevice(&dev)) != cudaSuccess) return rc;
+      if ((rc = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return rc;
+      if ((int64_t)s.L.batch * pl.C > 2 * (int64_t)nsm) kernel = (const void *)resident_kernel<T, 4>;
+    }
     rc = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (rc != cudaSuccess) return rc;
     if (pl.C > 8) {
