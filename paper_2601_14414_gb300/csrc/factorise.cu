@@ -10,6 +10,7 @@
 // and it copies G_k and e_k into the stage block.
 // Outputs are converted to the iteration precision T. LTI instances have two blocks: block 0
 // with H = (Qbar + rho I + rho Abar^T Abar)^{-1} and block 1 with the terminal H_{N-1}.
+#include "bl_slot.cuh"
 #include "launch.h"
 
 namespace pimpc {
@@ -172,28 +173,12 @@ __global__ void factorise_kernel(FactArgs a, T *blk) {
   // as wrapped 4 x 4 block diagonals (slot w is element (a, b) of block (d, I), see
   // bl_sym_index).
   auto put_sym_blocks = [&](int o, int m, const double *Xs, int ldx) {
-    const int nbm = bl_nb(m), Df = bl_full_diags(nbm), D0 = bl_diag_words(nbm);
-    const int full = 16 * nbm * (Df - 1);
+    const int nbm = bl_nb(m);
     for (int w = lane; w < bl_sym_words(m); w += 32) {
-      int I, d, a4, b;
-      if (w < D0) {  // slot t of the upper triangle of diagonal block I, or the padding
-        I = w / 10;
-        const int t = w - 10 * I;
-        a4 = t < 4 ? 0 : (t < 7 ? 1 : (t < 9 ? 2 : 3));
-        b = a4 + t - bl_tri(a4, a4);
-        d = 0;
-        if (I >= nbm) {
-          put(o + w, 0.0);
-          continue;
-        }
-      } else if (w < D0 + full) {
-        const int q = (w - D0) >> 2;
-        b = (w - D0) & 3;
-        I = q % nbm; d = 1 + (q / nbm) % (Df - 1); a4 = q / (nbm * (Df - 1));
-      } else {  // the middle block diagonal of an even nb, block rows I < nb/2
-        const int q = (w - D0 - full) >> 2, hb = nbm >> 1;
-        b = (w - D0 - full) & 3;
-        I = q % hb; d = hb; a4 = q / hb;
+      int d, I, a4, b;
+      if (!bl_sym_slot(nbm, w, d, I, a4, b)) {  // padding of the diagonal-block region
+        put(o + w, 0.0);
+        continue;
       }
       const int r = 4 * I + a4, c = 4 * ((I + d) % nbm) + b;
       put(o + w, (r < m && c < m) ? Xs[r * ldx + c] : 0.0);

@@ -1,15 +1,17 @@
 """The blocked stage-block layout (schedule family 5) checked on the CPU against the mathematics.
 
-The layout helpers of `csrc/pimpc_internal.cuh` are host-callable: a small C++ program compiled
-here with g++ includes that header and prints, for every matrix size m = 1..64, the block count,
-the number of stored block diagonals, the storage size and the storage index of every (block
-diagonal d, block row I, row a, column b) slot, plus the G strides and block offsets. The test
-then checks what the solve kernel relies on:
+The layout helpers of `csrc/pimpc_internal.cuh` and `csrc/bl_slot.cuh` are host-callable: a small
+C++ program compiled here with g++ includes them and prints, for every matrix size m = 1..64,
+the block count, the number of stored block diagonals, the storage size, the storage index of
+every (block diagonal d, block row I, row a, column b) slot and the slot decode of every storage
+word, plus the G strides and block offsets. The test then checks what the solve kernel and the
+factorisation rely on:
   * the storage index is injective into [0, bl_sym_words(m)) and leaves only the padding of the
-    diagonal-block region unused; the slots are exactly the upper triangles of the diagonal
-    blocks, the blocks S_{I,(I+d) mod nb} for 0 < d < nb/2 and, for d = nb/2, the block rows I
-    below nb/2 of an even nb (every element of a symmetric matrix once, up to symmetry); the
-    diagonal blocks' pairs and every other block row are aligned for the kernel's vector reads;
+    diagonal-block region unused, and the slot decode the factorisation writes through inverts
+    it; the slots are exactly the upper triangles of the diagonal blocks, the blocks
+    S_{I,(I+d) mod nb} for 0 < d < nb/2 and, for d = nb/2, the block rows I below nb/2 of an
+    even nb (every element of a symmetric matrix once, up to symmetry); the diagonal blocks'
+    pairs and every other block row are aligned for the kernel's vector reads;
   * storing those blocks holds every element of a symmetric m x m matrix;
   * the per-lane product the kernel runs (the diagonal block rebuilt from its upper triangle;
     per further full block diagonal: block (I, I+d) against h_{I+d}, the transpose of block
@@ -32,7 +34,7 @@ CUDA_INC = "/usr/local/cuda/include"
 
 HARNESS = r"""
 #include <cstdio>
-#include "pimpc_internal.cuh"
+#include "bl_slot.cuh"
 using namespace pimpc;
 int main() {
   for (int m = 1; m <= 64; ++m) {
@@ -44,6 +46,11 @@ int main() {
           for (int b = 0; b < 4; ++b)
             if (bl_sym_stored(nb, d, I, a, b))
               std::printf("S %d %d %d %d %d\n", d, I, a, b, bl_sym_index(nb, d, I, a, b));
+    for (int w = 0; w < bl_sym_words(m); ++w) {
+      int d, I, a, b;
+      const bool held = bl_sym_slot(nb, w, d, I, a, b);
+      std::printf("W %d %d %d %d %d %d\n", w, held ? 1 : 0, d, I, a, b);
+    }
   }
   for (int nx = 1; nx <= 40; ++nx)
     for (int nu = 1; nu <= 24; ++nu)
@@ -77,6 +84,9 @@ def layout(tmp_path_factory):
         elif f[0] == "S":
             dd, I, a, b, k = map(int, f[1:])
             cur["idx"][(dd, I, a, b)] = k
+        elif f[0] == "W":
+            w, held, dd, I, a, b = map(int, f[1:])
+            cur.setdefault("slot", {})[w] = (dd, I, a, b) if held else None
         else:
             blocks.append(tuple(map(int, f[1:])))
     return mats, blocks
@@ -108,6 +118,17 @@ def test_storage_index_is_a_bijection(layout):
         for (d, I, a, b), k in L["idx"].items():
             if d > 0:
                 assert (k - b) % 4 == 0 and L["idx"][(d, I, a, 0)] + b == k, (m, d, I, a, b)
+
+
+def test_slot_decode_inverts_the_storage_index(layout):
+    # bl_sym_slot (the factorisation writes every slot through it) returns, for each slot, the
+    # element whose storage index it is, and reports only the diagonal region's padding as empty
+    mats, _ = layout
+    for m, L in mats.items():
+        inv = {k: key for key, k in L["idx"].items()}
+        assert sorted(L["slot"]) == list(range(L["words"])), m
+        for w, key in L["slot"].items():
+            assert key == inv.get(w), (m, w, key)
 
 
 def stored(L, S):
