@@ -149,7 +149,8 @@ int pimpc_get_dynamics(pimpc_solver *s, double *A, double *B, double *e, int mem
  * pimpc_factorise -- the per-stage cache of Algorithm 1 in FP64: for every stage,
  *   H_k = (Qbar + rho I + rho Abar_{k+1}^T Abar_{k+1})^{-1} (k < N-1), H_{N-1} = (Qbar + rho I)^{-1}
  *   (definition after the velocity-form iteration) and M_k = (B_k^T B_k + I + Wdu / rho)^{-1},
- *   so that J_k v = M_k Bbar_k^T v, by Cholesky factorisation. Results are stored in the
+ *   so that J_k v = M_k Bbar_k^T v, inverted by Gauss-Jordan sweeps of the symmetric matrix in
+ *   pivot order (no pivoting: both matrices are positive definite). Results are stored in the
  *   iteration precision. pimpc_solve calls it implicitly when the cache is stale. With valid
  *   weights and rho both matrices are >= I (symmetric positive definite), so a non-positive
  *   pivot means non-finite or overflowing dynamics: the call stays asynchronous and the next
